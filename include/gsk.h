@@ -1,0 +1,182 @@
+/*
+ * gsk.h -- C ABI of libgsk, a GB300 (sm_103a) solver for the generalized
+ * shifted linear equations of Hoshi et al., "Extremely scalable algorithm
+ * for 10^8-atom quantum material simulation on the full system of the K
+ * computer" (SC16, arXiv:1609.08377).
+ *
+ * For every requested basis column j the library solves
+ *     (z_k B - A) x = e_j            for all shifts z_k          (Eq. EQ-SHIFT-EQ-J)
+ * with one Krylov subspace shared by all shifts (Sec. III-B), where A (the
+ * Hamiltonian) is real symmetric and B (the overlap) is symmetric positive
+ * definite (Sec. II-A, Eq. EQ-GEV-EQ). It returns the Green's-function
+ * elements G_ij(z_k) = [(z_k B - A)^{-1}]_ij (Eq. EQ-EIG-X=GB) for the rows
+ * i of A's pattern in column j (nearsightedness, Sec. II-B), and from them the
+ * density-matrix elements rho_ij by quadrature of Eq. EQ-DM-GREEN-FN with the
+ * Fermi function of Eq. EQ-FD-FUNC.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GSK_OK (0) or a negative GSK_E* code. No call traps,
+ *    aborts or exits; after an error the handle stays usable unless the error
+ *    is GSK_ECUDA with a sticky CUDA error.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the device that was current at gsk_create.
+ *  - Complex numbers are stored as interleaved pairs of doubles (re, im).
+ *  - Indices are 0-based and refer to the caller's original ordering.
+ *  - Calls on one handle are not thread safe; different handles are
+ *    independent.
+ */
+#ifndef GSK_H
+#define GSK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----- call-level status codes ----------------------------------------- */
+#define GSK_OK 0
+#define GSK_EINVAL (-1)     /* bad shape, index, pointer, option or non-finite value */
+#define GSK_ENOTSPD (-2)    /* B fails the positive-diagonal / diagonal-dominance check */
+#define GSK_ENOMEM (-3)     /* device or host allocation failed */
+#define GSK_ECUDA (-4)      /* a CUDA runtime call failed */
+#define GSK_ETIMEOUT (-5)   /* a bounded device wait gave up */
+#define GSK_ENOTSUP (-6)    /* option combination not supported by this build */
+
+/* ----- per-column status codes (status[] of gsk_solve) -------------------- */
+#define GSK_CONVERGED 0      /* every shift reached the residual tolerance */
+#define GSK_NOT_CONVERGED 1  /* max_iter reached; G holds the last iterate */
+#define GSK_BREAKDOWN 2      /* beta^2 <= 0 or a non-finite scalar (e.g. B not SPD) */
+#define GSK_TIMEOUT 3        /* the column was not finished within the step cap */
+
+/* ----- option values ------------------------------------------------------ */
+#define GSK_FP64 0           /* every product and vector update in FP64 */
+#define GSK_MIXED 1          /* FP32 inner B-solve, FP64 residual refinement, FP64 Lanczos */
+
+#define GSK_SCHED_FIFO 0     /* columns enter the work queue in the given order */
+#define GSK_SCHED_LEARNED 1  /* longest predicted iteration count first (needs a model) */
+
+typedef struct gsk_ctx* gsk_handle;
+
+/* Sparse symmetric matrix in CSR form (host memory, caller-owned, read only
+ * during gsk_create). row_ptr has n_rows+1 entries, col_idx/val row_ptr[n]
+ * entries; column indices within a row must be ascending and unique. */
+typedef struct {
+  int32_t n_rows;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+} gsk_csr;
+
+/* Orbital-block map (Sec. II-C: basis index i <-> (atom I, orbital alpha)).
+ * Atom I owns rows orb_offset[I] .. orb_offset[I] + orb_count[I] - 1; the
+ * offsets must tile 0..n_rows-1 in increasing order; orb_count is 1 or 4.
+ * pos (optional, may be NULL) holds 3*n_atoms coordinates used only to order
+ * atoms along a space-filling curve for memory locality. Host memory, read
+ * only during gsk_create. */
+typedef struct {
+  int32_t n_atoms;
+  const int32_t* orb_offset;
+  const int8_t* orb_count;
+  const double* pos;
+} gsk_orbmap;
+
+/* Solver options. Zero-initialise and set what you need; gsk_default_options
+ * fills the defaults listed here. */
+typedef struct {
+  int32_t precision;    /* GSK_FP64 (default) or GSK_MIXED */
+  double tol;           /* relative residual ||e_j - (z B - A) x||_2 for every shift; default 1e-8 */
+  int32_t max_iter;     /* Lanczos steps per column; default 20000 */
+  int32_t batch_w;      /* lanes (columns in flight): 32, 64 or 128; 0 = autotune (default) */
+  int32_t refine;       /* GSK_MIXED only: 1 = FP64 residual correction of each B-solve (default), 0 = none */
+  int32_t sched;        /* GSK_SCHED_FIFO (default) or GSK_SCHED_LEARNED */
+  double inner_tol;     /* relative residual of each B-solve; 0 = default (1e-12 FP64, 1e-6 per FP32 pass) */
+  int32_t max_inner;    /* CG iteration cap per B-solve pass; default 200 */
+  int32_t use_graph;    /* 1 = run the solve as one captured CUDA graph with device-side loops (default) */
+  void* stream;         /* cudaStream_t to run on; NULL = the legacy default stream */
+} gsk_options;
+
+/* Fill *opt with the defaults above. */
+void gsk_default_options(gsk_options* opt);
+
+/* Build a solver handle from A, B (same pattern, symmetric) and the orbital
+ * map. Copies the matrices to the device in the library's block layout
+ * (FP64, plus an FP32 copy for GSK_MIXED). Returns GSK_EINVAL for malformed
+ * input or non-finite values, GSK_ENOTSPD when some B_ii <= 0 or a row of B is
+ * not strictly diagonally dominant (a sufficient test for positive
+ * definiteness; the library requires it). The handle owns every device
+ * buffer; *out is NULL on failure. The current CUDA device is bound to the
+ * handle. */
+int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_handle* out);
+
+/* Release the handle and all its device memory. Accepts NULL. */
+int gsk_destroy(gsk_handle h);
+
+/* Matrix dimension M and number of stored entries of A. */
+int gsk_dims(gsk_handle h, int32_t* M, int64_t* nnz);
+
+/* offsets[c] = sum_{c' < c} |P(cols[c'])| for c = 0..n_cols, where P(j) is the
+ * pattern of column j of A (host arrays). This is the layout of G and rho:
+ * element (i, c, k) with i the t-th entry of CSR row cols[c] of A lives at
+ * (offsets[c] + t) * n_shifts + k. */
+int gsk_pattern_offsets(gsk_handle h, int32_t n_cols, const int32_t* cols, int64_t* offsets);
+
+/* Solve (z_k B - A) x = e_j for j in cols and every shift, with the shifted
+ * B-inner-product Lanczos method (one Krylov subspace per column shared by
+ * all shifts, Sec. III-B), and write G_ij(z_k) for i in P(j).
+ *
+ *   n_shifts  S >= 1
+ *   z         host, 2*S doubles: shifts (re, im); Im z_k > 0 required unless
+ *             eta is given
+ *   eta       host, n_cols doubles or NULL: if given, column c uses the
+ *             shifts Re z_k + i*eta[c] (eta[c] > 0)
+ *   cols      host, n_cols distinct column indices in [0, M)
+ *   G         device (or host) buffer of offsets[n_cols]*S complex doubles
+ *             (see gsk_pattern_offsets); host buffers are staged through
+ *             device memory
+ *   iters     host, n_cols: Lanczos steps taken per column (may be NULL)
+ *   status    host, n_cols: GSK_CONVERGED ... per column (may be NULL)
+ *   resid     host, n_cols: max over shifts of the residual estimate (may be NULL)
+ *
+ * The call is synchronous: it returns after the results are written.
+ * Returns GSK_EINVAL for bad arguments (nothing is written). */
+int gsk_solve(gsk_handle h, int32_t n_shifts, const double* z, const double* eta,
+              int32_t n_cols, const int32_t* cols, const gsk_options* opt,
+              double* G, int32_t* iters, int32_t* status, double* resid);
+
+/* rho_ij = -(1/pi) * sum_k w_k f(eps_k) Im G_ij(z_k) on the same layout as G
+ * (Eq. EQ-DM-GREEN-FN by quadrature; f(e) = 1/(1+exp((e-mu)/kT)),
+ * Eq. EQ-FD-FUNC, evaluated without overflow).
+ *   eps, w    host, S doubles: real parts of the shifts and quadrature weights
+ *   G         device, n_elem*S complex doubles; rho device, n_elem doubles
+ *   stream    cudaStream_t or NULL. Asynchronous on that stream. */
+int gsk_density(gsk_handle h, int64_t n_elem, int32_t n_shifts, const double* eps,
+                const double* w, double mu, double kT, const double* G, double* rho,
+                void* stream);
+
+/* Tr over the column set of rho X (Eq. TRACE-X restricted to the columns
+ * solved): sum_c sum_{t} rho[offsets[c]+t] * X_{cols[c], i_t}, X = A (which=0)
+ * or B (which=1). rho device; result written to *out (host). Synchronous. */
+int gsk_trace(gsk_handle h, int32_t n_cols, const int32_t* cols, const double* rho,
+              int32_t which, double* out);
+
+/* Counters of the last gsk_solve on this handle. */
+typedef struct {
+  int64_t outer_steps;       /* Lanczos steps of the lane batch (lock-step) */
+  int64_t cg_iterations;     /* inner CG iterations, all B-solve passes */
+  int64_t kernel_launches;   /* kernels the solve launched (graph nodes executed) */
+  int32_t batch_w;           /* lanes used */
+  int32_t used_graph;        /* 1 when the solve ran as one CUDA graph */
+} gsk_stats;
+
+/* Copy the counters of the last gsk_solve into *out (host). */
+int gsk_last_stats(gsk_handle h, gsk_stats* out);
+
+/* Human-readable text for a GSK_* code. */
+const char* gsk_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSK_H */

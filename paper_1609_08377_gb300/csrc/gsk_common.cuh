@@ -1,0 +1,252 @@
+// Shared device definitions of libgsk: block layout of the pencil, lane
+// control block, vector load helpers and the deterministic two-level lane
+// reduction used by every kernel that produces per-column inner products.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsk.h"
+
+namespace gsk {
+
+constexpr int kThreads = 256;             // threads per CTA of the row kernels
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxW = 128;                // widest lane batch
+constexpr int kMaxShifts = 1024;          // shifts per solve (shared-memory bound of the shift kernel)
+
+// ---------------------------------------------------------------------------
+// Block layout of A and B (identical pattern), atoms in the library's order.
+// Atom I owns rows atom_roff[I] .. atom_roff[I] + atom_orb[I] - 1. Its
+// neighbour entries nbr_ptr[I] .. nbr_ptr[I+1] list first the 4-orbital
+// neighbours (up to nbr_mid[I]) then the 1-orbital ones; an entry stores the
+// neighbour's first row. The values of atom I start at val_ptr[I] (a multiple
+// of 4) and are, per 4-orbital neighbour, 4 columns of o_I values (column b
+// holds rows a = 0..o_I-1), then per 1-orbital neighbour o_I values for a
+// 4-orbital atom, or, for a 1-orbital atom, one value per neighbour with the
+// 1-orbital neighbours padded to a multiple of 4 (padding: value 0, row of
+// the atom itself).
+// ---------------------------------------------------------------------------
+struct Layout {
+  int32_t n_atoms;
+  int32_t M;
+  int32_t chunk;                 // atoms per CTA in the row kernels
+  int32_t n_ctas;                // CTAs of the row kernels
+  const int32_t* atom_roff;      // n_atoms + 1
+  const int8_t* atom_orb;        // n_atoms
+  const int32_t* nbr_ptr;        // n_atoms + 1
+  const int32_t* nbr_mid;        // n_atoms
+  const int32_t* nbr_roff;       // neighbour entries
+  const int64_t* val_ptr;        // n_atoms
+};
+
+// Lane states of the batched solver.
+enum LaneState : int { LS_IDLE = 0, LS_SEED = 1, LS_ACTIVE = 2 };
+
+// Finalisation applied by the last CTA of a reducing kernel to the per-lane sums.
+enum Fin : int {
+  FIN_ALPHA = 0,     // alpha_n = q.(A q)
+  FIN_UNORM = 1,     // ||u||^2 -> unorm, start of a B-solve
+  FIN_CG_A = 2,      // p.(B p) -> CG step length
+  FIN_CG_RR = 3,     // r.r -> CG direction update, convergence
+  FIN_RESID = 4,     // ||u - B v0||^2 -> start of the refinement B-solve
+  FIN_BETA = 5,      // u.v -> beta_n, lane bookkeeping, refill from the queue
+  FIN_SUM = 6,       // plain sums into red_out
+};
+
+// Per-lane control block in device memory (structure of arrays, kMaxW each)
+// plus solve-wide counters. All fields are written only by the single last
+// CTA of a reducing kernel, by the prime kernel, or by split 0 of the shift
+// kernel, so no two writers race.
+struct LaneCtl {
+  int* job;            // job index of the lane, -1 when idle
+  int* state;          // LaneState
+  int* n;              // completed Lanczos steps of the current column
+  int* done;           // set by the shift kernel when the column finished this step
+  int* brk;            // breakdown seen (beta^2 <= 0, non-finite, inner solve failed)
+  double* alpha;       // alpha_n of the current step
+  double* beta_prev;   // beta_{n-1} (off-diagonal entering step n)
+  double* beta0;       // ||b||_B of the seed
+  double* unorm;       // ||u_n||_2
+  double* inv_beta;    // scale applied by the finish kernel (0 zeroes the lane)
+  double* rr;          // CG: current r.r
+  double* rr_target;   // CG: stop when r.r <= rr_target
+  double* cg_a;        // CG step length
+  double* cg_b;        // CG direction coefficient
+  int* cg_on;          // CG still iterating for this lane
+  double* red_out;     // FIN_SUM results
+  // solve-wide
+  int* queue_head;     // next queue slot to hand out
+  int* cg_iter;        // CG iterations of the current B-solve pass
+  int* step;           // outer steps executed
+  int* unfinished;     // lanes busy + jobs queued
+  int* cg_total;       // total CG iterations (all passes), for statistics
+  unsigned int* red_counter;   // arrival counter of the last-CTA reduction
+  double* partials;            // n_ctas * W partial sums
+};
+
+// Read-only description of the job list of one solve.
+struct Jobs {
+  int32_t n_jobs;
+  const int32_t* queue;       // queue order -> job index
+  const int32_t* col_row;     // job -> row (library order) of e_j
+  const double* eta;          // job -> damping of its shifts
+};
+
+// Graph control: conditional handles set from device code (0 when the solve
+// is driven from the host).
+struct GraphCtl {
+  int use_graph;
+  cudaGraphConditionalHandle h_outer;
+  cudaGraphConditionalHandle h_inner1;
+  cudaGraphConditionalHandle h_inner2;
+  int max_inner;
+  int step_cap;
+};
+
+// ---------------------------------------------------------------------------
+// Vector helpers: L consecutive lanes of one row.
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+struct LaneVec;
+template <> struct LaneVec<float, 1> { using V = float; };
+template <> struct LaneVec<float, 2> { using V = float2; };
+template <> struct LaneVec<float, 4> { using V = float4; };
+template <> struct LaneVec<double, 1> { using V = double; };
+template <> struct LaneVec<double, 2> { using V = double2; };
+
+template <typename T, int L>
+__device__ __forceinline__ void ld_lanes(const T* __restrict__ p, T (&o)[L]) {
+  if constexpr (L == 4 && sizeof(T) == 8) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  } else {
+    using V = typename LaneVec<T, L>::V;
+    const V v = *reinterpret_cast<const V*>(p);
+    const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < L; ++i) o[i] = e[i];
+  }
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void st_lanes(T* __restrict__ p, const T (&o)[L]) {
+  if constexpr (L == 4 && sizeof(T) == 8) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+  } else {
+    using V = typename LaneVec<T, L>::V;
+    V v;
+    T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int i = 0; i < L; ++i) e[i] = o[i];
+    *reinterpret_cast<V*>(p) = v;
+  }
+}
+
+// Four consecutive matrix values (16-byte aligned for float, 32 for double).
+template <typename T>
+struct Quad { T x, y, z, w; };
+
+__device__ __forceinline__ Quad<float> ld_quad(const float* __restrict__ p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> ld_quad(const double* __restrict__ p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+
+// ---------------------------------------------------------------------------
+// Complex helpers (double2 = re, im). Division by Smith's method
+// (R. L. Smith, CACM 5(8), 1962), which avoids overflow of c^2 + d^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double r = b.y / b.x;
+    const double den = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  } else {
+    const double r = b.x / b.y;
+    const double den = b.x * r + b.y;
+    return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+  }
+}
+__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
+
+// ---------------------------------------------------------------------------
+// Per-lane reduction: every thread holds partial sums for its L lanes
+// (lanes lane0 .. lane0+L-1). The CTA folds its warps in a fixed order and
+// writes one partial per lane; the last CTA to arrive folds all partials in
+// CTA order and applies the finalisation. Deterministic: the summation order
+// never depends on timing.
+// ---------------------------------------------------------------------------
+struct RedArgs {
+  LaneCtl c;
+  Jobs jobs;
+  GraphCtl gc;
+  int fin;
+  int W;
+  double inner_tol2;     // squared relative tolerance of the B-solve pass
+  int max_iter;
+};
+
+__device__ void finalize_lane(const RedArgs& r, int lane, double s);
+__device__ void finalize_all(const RedArgs& r);
+
+template <int L>
+__device__ __forceinline__ void lane_reduce_commit(const double (&mine)[L], const RedArgs& r) {
+  __shared__ double sm[kWarps][kMaxW];
+  __shared__ bool is_last;
+  const int W = r.W;
+  const int warp = threadIdx.x >> 5;
+  const int lane0 = (threadIdx.x & 31) * L;
+#pragma unroll
+  for (int i = 0; i < L; ++i) sm[warp][lane0 + i] = mine[i];
+  __syncthreads();
+  if (threadIdx.x < W) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += sm[w][threadIdx.x];
+    r.c.partials[(size_t)blockIdx.x * W + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(r.c.red_counter, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int parts = kThreads / W;
+  const int l = threadIdx.x % W;
+  const int pidx = threadIdx.x / W;
+  double s = 0.0;
+  if (pidx < parts) {
+    for (int b = pidx; b < (int)gridDim.x; b += parts) s += __ldcg(&r.c.partials[(size_t)b * W + l]);
+  }
+  __syncthreads();
+  if (pidx < parts) sm[pidx][l] = s;
+  __syncthreads();
+  if (threadIdx.x < W) {
+    double t = 0.0;
+    for (int p = 0; p < parts; ++p) t += sm[p][threadIdx.x];
+    finalize_lane(r, threadIdx.x, t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    finalize_all(r);
+    *r.c.red_counter = 0u;
+  }
+}
+
+}  // namespace gsk

@@ -1,0 +1,83 @@
+// Host-side handle of libgsk (shared by the translation units of the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "gsk_common.cuh"
+
+namespace gsk {
+
+// Device buffer that grows on demand and is owned by the handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(ptr); }
+};
+
+}  // namespace gsk
+
+struct gsk_ctx {
+  int device = 0;
+  int32_t M = 0;
+  int32_t n_atoms = 0;
+  int64_t nnz = 0;        // stored entries of A (caller's pattern)
+  int64_t n_vals = 0;     // values in the block layout (with padding)
+  int32_t n_nbr = 0;      // neighbour entries of the block layout
+  int num_sms = 0;
+
+  // host-side maps
+  std::vector<int64_t> row_ptr;     // caller's CSR pattern of A
+  std::vector<int32_t> col_idx;
+  std::vector<int32_t> row_lib;     // caller row -> library row
+  std::vector<int64_t> csr_vpos;    // caller CSR entry -> value slot (block layout)
+  std::vector<int32_t> atom_perm;   // library atom -> caller atom
+  std::vector<int8_t> orb_lib;      // library atom -> orbital count
+  std::vector<double> pos_lib;      // library atom -> xyz (empty without positions)
+  std::vector<double> a_diag, b_diag, a_rowabs, b_rowabs;   // per caller row
+
+  // device block layout
+  gsk::Layout lay{};
+  gsk::DevBuf d_atom_roff, d_atom_orb, d_nbr_ptr, d_nbr_mid, d_nbr_roff, d_val_ptr;
+  gsk::DevBuf d_A64, d_B64, d_A32, d_B32;
+
+  gsk_stats last{};
+
+  // solver workspace (grown on demand)
+  gsk::DevBuf ws_vec;      // Lanczos / CG vectors
+  gsk::DevBuf ws_lane;     // lane control block
+  gsk::DevBuf ws_jobs;     // job arrays
+  gsk::DevBuf ws_shift;    // shift recurrence state
+  gsk::DevBuf ws_gstage;   // staging of G for host output buffers
+  gsk::DevBuf ws_misc;     // density / trace scratch
+
+  ~gsk_ctx() {
+    gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr,
+                          &d_A64, &d_B64, &d_A32, &d_B32, &ws_vec, &ws_lane, &ws_jobs,
+                          &ws_shift, &ws_gstage, &ws_misc};
+    for (auto* b : all) b->release();
+  }
+};
+
+namespace gsk {
+int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols,
+               const int32_t* cols, const gsk_options* opt, double* G, int32_t* iters,
+               int32_t* status, double* resid);
+}

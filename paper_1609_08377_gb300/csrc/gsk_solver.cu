@@ -1,0 +1,1332 @@
+// Batched shifted B-Lanczos solver of libgsk (device kernels + orchestration).
+//
+// Method (Sec. III-A/III-B of the paper: generalized shifted equations
+// (z B - A) x = e_j solved with one Krylov subspace for all shifts). With
+// H = B^{-1} A, self-adjoint in <x, y>_B = x^T B y, the equations become
+// (z I - H) x = B^{-1} e_j. A Lanczos process on H started from B^{-1} e_j
+// keeps q_n and B q_n:
+//   seed:   u = e_j, v = B^{-1} u, beta_0 = sqrt(u.v), q_1 = v/beta_0, Bq_1 = u/beta_0
+//   step n: w = A q_n, alpha_n = q_n.w, u = w - alpha_n Bq_n - beta_{n-1} Bq_{n-1},
+//           v = B^{-1} u (inner CG), beta_n = sqrt(u.v), q_{n+1} = v/beta_n,
+//           Bq_{n+1} = u/beta_n.
+// For every shift sigma_k the solution x_n = Q_n (sigma_k - T_n)^{-1} beta_0 e_1
+// is updated by the LDL^T ("direct Lanczos") recurrence of sigma_k I - T_n:
+//   d_1 = sigma - alpha_1, g_1 = beta_0;  l_{n-1} = -beta_{n-1}/d_{n-1},
+//   d_n = sigma - alpha_n + l_{n-1} beta_{n-1}, g_n = -l_{n-1} g_{n-1},
+//   zeta_n = g_n/d_n, p_n = q_n - l_{n-1} p_{n-1}, x_n = x_{n-1} + zeta_n p_n,
+// restricted to the rows of A's pattern in column j (Sec. II-B). The
+// residual of shift k after step n is |zeta_n| * ||u_n||_2 because
+// e_j - (sigma B - A) x_n = zeta_n u_n. Im sigma != 0 keeps every d_n away
+// from zero (Im d_n >= Im sigma), so the recurrence cannot break down.
+//
+// Columns are independent (Eq. TRACE-X-DECOMP); W of them run as lanes of one
+// batch in lock step, and a lane whose column finishes takes the next job
+// from a device work queue at the end of the step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gsk_common.cuh"
+#include "gsk_ctx.h"
+
+namespace gsk {
+
+// ===========================================================================
+// Finalisation of per-lane sums (runs in the last CTA of a reducing kernel)
+// ===========================================================================
+__device__ void finalize_lane(const RedArgs& r, int l, double s) {
+  const LaneCtl& c = r.c;
+  switch (r.fin) {
+    case FIN_ALPHA:
+      c.alpha[l] = s;
+      break;
+    case FIN_UNORM: {
+      const int st = c.state[l];
+      c.unorm[l] = sqrt(s);
+      c.rr[l] = s;
+      c.rr_target[l] = r.inner_tol2 * s;
+      c.cg_a[l] = 0.0;
+      c.cg_b[l] = 0.0;
+      c.cg_on[l] = (st != LS_IDLE && !c.brk[l] && s > 0.0 && isfinite(s)) ? 1 : 0;
+      break;
+    }
+    case FIN_CG_A:
+      if (c.cg_on[l]) {
+        if (s > 0.0 && isfinite(s)) {
+          c.cg_a[l] = c.rr[l] / s;
+        } else {            // p.Bp <= 0: B is not positive definite for this lane
+          c.cg_a[l] = 0.0;
+          c.cg_on[l] = 0;
+          c.brk[l] = 1;
+        }
+      } else {
+        c.cg_a[l] = 0.0;
+      }
+      break;
+    case FIN_CG_RR:
+      if (c.cg_on[l]) {
+        if (!isfinite(s)) {
+          c.cg_b[l] = 0.0;
+          c.cg_on[l] = 0;
+          c.brk[l] = 1;
+        } else {
+          c.cg_b[l] = s / c.rr[l];
+          c.rr[l] = s;
+          if (s <= c.rr_target[l]) c.cg_on[l] = 0;
+        }
+      } else {
+        c.cg_b[l] = 0.0;
+      }
+      break;
+    case FIN_RESID: {
+      const int st = c.state[l];
+      c.rr[l] = s;
+      c.rr_target[l] = r.inner_tol2 * s;
+      c.cg_a[l] = 0.0;
+      c.cg_b[l] = 0.0;
+      c.cg_on[l] = (st != LS_IDLE && !c.done[l] && !c.brk[l] && s > 0.0 && isfinite(s)) ? 1 : 0;
+      break;
+    }
+    case FIN_BETA: {
+      const int st = c.state[l];
+      if (st == LS_ACTIVE) {
+        if (c.done[l]) {
+          c.inv_beta[l] = 0.0;
+        } else if (!c.brk[l] && s > 0.0 && isfinite(s)) {
+          const double b = sqrt(s);
+          c.beta_prev[l] = b;
+          c.inv_beta[l] = 1.0 / b;
+          c.n[l] += 1;
+        } else {
+          c.brk[l] = 1;
+          c.inv_beta[l] = 0.0;
+          c.n[l] += 1;
+        }
+      } else if (st == LS_SEED) {
+        c.state[l] = LS_ACTIVE;
+        c.n[l] = 0;
+        c.beta_prev[l] = 0.0;
+        if (!c.brk[l] && s > 0.0 && isfinite(s)) {
+          const double b0 = sqrt(s);
+          c.beta0[l] = b0;
+          c.inv_beta[l] = 1.0 / b0;
+        } else {
+          c.brk[l] = 1;
+          c.inv_beta[l] = 0.0;
+        }
+      } else {
+        c.inv_beta[l] = 0.0;
+      }
+      break;
+    }
+    case FIN_SUM:
+    default:
+      c.red_out[l] = s;
+      break;
+  }
+}
+
+__device__ __forceinline__ void set_cond(const GraphCtl& gc, cudaGraphConditionalHandle h, int v) {
+  if (gc.use_graph) cudaGraphSetConditional(h, v ? 1u : 0u);
+}
+
+// Solve-wide bookkeeping after the per-lane finalisation (thread 0 of the last
+// CTA). The CG kernels of the refinement pass carry max_iter == -1 in their
+// RedArgs, which selects the conditional handle of the second inner loop.
+__device__ void finalize_all(const RedArgs& r) {
+  const LaneCtl& c = r.c;
+  const int W = r.W;
+  switch (r.fin) {
+    case FIN_UNORM: {
+      *c.cg_iter = 0;
+      int any = 0;
+      for (int l = 0; l < W; ++l) any += c.cg_on[l];
+      *c.unfinished = any;
+      set_cond(r.gc, r.gc.h_inner1, any > 0);
+      break;
+    }
+    case FIN_RESID: {
+      *c.cg_iter = 0;
+      int any = 0;
+      for (int l = 0; l < W; ++l) any += c.cg_on[l];
+      *c.unfinished = any;
+      set_cond(r.gc, r.gc.h_inner2, any > 0);
+      break;
+    }
+    case FIN_CG_RR: {
+      const int it = ++(*c.cg_iter);
+      ++(*c.cg_total);
+      int any = 0;
+      for (int l = 0; l < W; ++l) any += c.cg_on[l];
+      if (any > 0 && it >= r.gc.max_inner) {       // inner solve failed to converge
+        for (int l = 0; l < W; ++l)
+          if (c.cg_on[l]) {
+            c.cg_on[l] = 0;
+            c.brk[l] = 1;
+          }
+        any = 0;
+      }
+      *c.unfinished = any;
+      set_cond(r.gc, r.max_iter == -1 ? r.gc.h_inner2 : r.gc.h_inner1, any > 0);
+      break;
+    }
+    case FIN_BETA: {
+      const int step = ++(*c.step);
+      int qh = *c.queue_head;
+      int busy = 0;
+      for (int l = 0; l < W; ++l) {
+        const int st = c.state[l];
+        if ((st == LS_ACTIVE && c.done[l]) || st == LS_IDLE) {
+          if (qh < r.jobs.n_jobs) {
+            c.job[l] = r.jobs.queue[qh++];
+            c.state[l] = LS_SEED;
+          } else {
+            c.job[l] = -1;
+            c.state[l] = LS_IDLE;
+          }
+          c.done[l] = 0;
+          c.brk[l] = 0;
+          c.n[l] = 0;
+          c.inv_beta[l] = 0.0;
+        }
+        busy += (c.state[l] != LS_IDLE);
+      }
+      *c.queue_head = qh;
+      const int unfinished = busy + (r.jobs.n_jobs - qh);
+      *c.unfinished = unfinished;
+      set_cond(r.gc, r.gc.h_outer, unfinished > 0 && step < r.gc.step_cap);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ===========================================================================
+// K1: block SpMM  Y[:, lanes] = S X[:, lanes]  (S = A or B, W lanes)
+// ===========================================================================
+enum SpmmMode : int { SP_DOT = 0, SP_RESID = 1 };
+
+template <typename TV, typename TX, typename TY>
+struct SpmmArgs {
+  Layout g;
+  const TV* val;
+  const TX* X;
+  TY* Y;
+  const double* U;   // SP_RESID: right-hand side u (FP64)
+  TY* P;             // SP_RESID: CG direction, set to the residual
+  TY* Z;             // SP_RESID: CG solution, set to zero
+  RedArgs red;
+};
+
+template <typename T>
+__device__ __forceinline__ T fmadd(T a, T b, T c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Product of one atom's block row with W lanes of X; acc[a][i] for row a, lane lane0+i.
+template <typename TV, typename TX, typename TA, int L>
+__device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __restrict__ val,
+                                                 const TX* __restrict__ X, int W, int lane0, int I,
+                                                 TA (&acc)[4][L], int& oI, int& r0) {
+  oI = g.atom_orb[I];
+  r0 = g.atom_roff[I];
+  const TV* v = val + g.val_ptr[I];
+  int e = g.nbr_ptr[I];
+  const int em = g.nbr_mid[I];
+  const int e1 = g.nbr_ptr[I + 1];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc[a][i] = TA(0);
+  if (oI == 4) {
+    for (; e < em; ++e) {
+      const TX* xp = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
+      TX x0[L], x1[L], x2[L], x3[L];
+      ld_lanes<TX, L>(xp, x0);
+      ld_lanes<TX, L>(xp + W, x1);
+      ld_lanes<TX, L>(xp + 2 * W, x2);
+      ld_lanes<TX, L>(xp + 3 * W, x3);
+      const Quad<TV> c0 = ld_quad(v), c1 = ld_quad(v + 4), c2 = ld_quad(v + 8), c3 = ld_quad(v + 12);
+      v += 16;
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const TA y0 = TA(x0[i]), y1 = TA(x1[i]), y2 = TA(x2[i]), y3 = TA(x3[i]);
+        acc[0][i] = fmadd<TA>(TA(c0.x), y0, fmadd<TA>(TA(c1.x), y1, fmadd<TA>(TA(c2.x), y2, fmadd<TA>(TA(c3.x), y3, acc[0][i]))));
+        acc[1][i] = fmadd<TA>(TA(c0.y), y0, fmadd<TA>(TA(c1.y), y1, fmadd<TA>(TA(c2.y), y2, fmadd<TA>(TA(c3.y), y3, acc[1][i]))));
+        acc[2][i] = fmadd<TA>(TA(c0.z), y0, fmadd<TA>(TA(c1.z), y1, fmadd<TA>(TA(c2.z), y2, fmadd<TA>(TA(c3.z), y3, acc[2][i]))));
+        acc[3][i] = fmadd<TA>(TA(c0.w), y0, fmadd<TA>(TA(c1.w), y1, fmadd<TA>(TA(c2.w), y2, fmadd<TA>(TA(c3.w), y3, acc[3][i]))));
+      }
+    }
+    for (; e < e1; ++e) {
+      const TX* xp = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
+      TX x0[L];
+      ld_lanes<TX, L>(xp, x0);
+      const Quad<TV> c0 = ld_quad(v);
+      v += 4;
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const TA y0 = TA(x0[i]);
+        acc[0][i] = fmadd<TA>(TA(c0.x), y0, acc[0][i]);
+        acc[1][i] = fmadd<TA>(TA(c0.y), y0, acc[1][i]);
+        acc[2][i] = fmadd<TA>(TA(c0.z), y0, acc[2][i]);
+        acc[3][i] = fmadd<TA>(TA(c0.w), y0, acc[3][i]);
+      }
+    }
+  } else {
+    for (; e < em; ++e) {
+      const TX* xp = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
+      TX x0[L], x1[L], x2[L], x3[L];
+      ld_lanes<TX, L>(xp, x0);
+      ld_lanes<TX, L>(xp + W, x1);
+      ld_lanes<TX, L>(xp + 2 * W, x2);
+      ld_lanes<TX, L>(xp + 3 * W, x3);
+      const Quad<TV> c0 = ld_quad(v);
+      v += 4;
+#pragma unroll
+      for (int i = 0; i < L; ++i)
+        acc[0][i] = fmadd<TA>(TA(c0.x), TA(x0[i]), fmadd<TA>(TA(c0.y), TA(x1[i]),
+                    fmadd<TA>(TA(c0.z), TA(x2[i]), fmadd<TA>(TA(c0.w), TA(x3[i]), acc[0][i]))));
+    }
+    for (; e < e1; e += 4) {
+      const TX* xa = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
+      const TX* xb = X + (size_t)__ldg(&g.nbr_roff[e + 1]) * W + lane0;
+      const TX* xc = X + (size_t)__ldg(&g.nbr_roff[e + 2]) * W + lane0;
+      const TX* xd = X + (size_t)__ldg(&g.nbr_roff[e + 3]) * W + lane0;
+      TX x0[L], x1[L], x2[L], x3[L];
+      ld_lanes<TX, L>(xa, x0);
+      ld_lanes<TX, L>(xb, x1);
+      ld_lanes<TX, L>(xc, x2);
+      ld_lanes<TX, L>(xd, x3);
+      const Quad<TV> c0 = ld_quad(v);
+      v += 4;
+#pragma unroll
+      for (int i = 0; i < L; ++i)
+        acc[0][i] = fmadd<TA>(TA(c0.x), TA(x0[i]), fmadd<TA>(TA(c0.y), TA(x1[i]),
+                    fmadd<TA>(TA(c0.z), TA(x2[i]), fmadd<TA>(TA(c0.w), TA(x3[i]), acc[0][i]))));
+    }
+  }
+}
+
+template <typename TV, typename TX, typename TY, typename TA, int L, int MODE>
+__global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const int warp = threadIdx.x >> 5;
+  TA dot[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) dot[i] = TA(0);
+  const int a0 = blockIdx.x * a.g.chunk;
+  const int a1 = min(a0 + a.g.chunk, a.g.n_atoms);
+  for (int I = a0 + warp; I < a1; I += kWarps) {
+    TA acc[4][L];
+    int oI, r0;
+    atom_row_product<TV, TX, TA, L>(a.g, a.val, a.X, W, lane0, I, acc, oI, r0);
+    for (int r = 0; r < oI; ++r) {
+      const size_t base = (size_t)(r0 + r) * W + lane0;
+      TY y[L];
+      if constexpr (MODE == SP_DOT) {
+#pragma unroll
+        for (int i = 0; i < L; ++i) y[i] = TY(acc[r][i]);
+        st_lanes<TY, L>(a.Y + base, y);
+        TX xo[L];
+        ld_lanes<TX, L>(a.X + base, xo);
+#pragma unroll
+        for (int i = 0; i < L; ++i) dot[i] = fmadd<TA>(TA(xo[i]), TA(y[i]), dot[i]);
+      } else {
+        double uu[L];
+        ld_lanes<double, L>(a.U + base, uu);
+        TY z[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          y[i] = TY(uu[i] - double(acc[r][i]));
+          z[i] = TY(0);
+          dot[i] = fmadd<TA>(TA(y[i]), TA(y[i]), dot[i]);
+        }
+        st_lanes<TY, L>(a.Y + base, y);
+        st_lanes<TY, L>(a.P + base, y);
+        st_lanes<TY, L>(a.Z + base, z);
+      }
+    }
+  }
+  double d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = double(dot[i]);
+  lane_reduce_commit<L>(d, a.red);
+}
+
+// ===========================================================================
+// Vector kernels over all rows (warp per row, L lanes per thread)
+// ===========================================================================
+struct VecArgs {
+  int M;
+  double* q;
+  double* ring0;
+  double* ring1;
+  double* u;       // holds w = A q on entry of the update kernel, u afterwards
+  void* r;
+  void* p;
+  void* Bp;
+  void* x;         // CG solution of the current pass (v, or v0 in mixed mode)
+  void* x2;        // mixed mode: refinement correction d
+  const int* step;
+  RedArgs red;
+};
+
+__device__ __forceinline__ int vec_warp_id() { return blockIdx.x * kWarps + (threadIdx.x >> 5); }
+__device__ __forceinline__ int vec_warp_count() { return gridDim.x * kWarps; }
+
+// K_U: three-term update (or seed / idle), start of the B-solve, ||u||^2.
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads) k_update(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const LaneCtl& c = a.red.c;
+  int st[L], jr[L];
+  double al[L], bp[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int l = lane0 + i;
+    st[i] = c.state[l];
+    al[i] = c.alpha[l];
+    bp[i] = c.beta_prev[l];
+    jr[i] = (st[i] == LS_SEED) ? a.red.jobs.col_row[c.job[l]] : -1;
+  }
+  const int slot = (*a.step) & 1;
+  const double* Bq = slot ? a.ring1 : a.ring0;
+  const double* Bqm = slot ? a.ring0 : a.ring1;
+  T* r = static_cast<T*>(a.r);
+  T* p = static_cast<T*>(a.p);
+  T* x = static_cast<T*>(a.x);
+  T acc[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) acc[i] = T(0);
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    double w[L], b1[L], b2[L], uu[L];
+    ld_lanes<double, L>(a.u + base, w);
+    ld_lanes<double, L>(Bq + base, b1);
+    ld_lanes<double, L>(Bqm + base, b2);
+    T ut[L], zero[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      if (st[i] == LS_ACTIVE)
+        uu[i] = fma(-al[i], b1[i], fma(-bp[i], b2[i], w[i]));
+      else if (st[i] == LS_SEED)
+        uu[i] = (row == jr[i]) ? 1.0 : 0.0;
+      else
+        uu[i] = 0.0;
+      ut[i] = T(uu[i]);
+      zero[i] = T(0);
+      acc[i] = fmadd<T>(ut[i], ut[i], acc[i]);
+    }
+    st_lanes<double, L>(a.u + base, uu);
+    st_lanes<T, L>(r + base, ut);
+    st_lanes<T, L>(p + base, ut);
+    st_lanes<T, L>(x + base, zero);
+  }
+  double d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = double(acc[i]);
+  lane_reduce_commit<L>(d, a.red);
+}
+
+// K_C: x += a p, r -= a Bp, r.r
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads) k_cg_update(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  T ca[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) ca[i] = T(a.red.c.cg_a[lane0 + i]);
+  T* r = static_cast<T*>(a.r);
+  const T* p = static_cast<const T*>(a.p);
+  const T* Bp = static_cast<const T*>(a.Bp);
+  T* x = static_cast<T*>(a.x);
+  T acc[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) acc[i] = T(0);
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    T pv[L], bv[L], xv[L], rv[L];
+    ld_lanes<T, L>(p + base, pv);
+    ld_lanes<T, L>(Bp + base, bv);
+    ld_lanes<T, L>(x + base, xv);
+    ld_lanes<T, L>(r + base, rv);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      xv[i] = fmadd<T>(ca[i], pv[i], xv[i]);
+      rv[i] = fmadd<T>(-ca[i], bv[i], rv[i]);
+      acc[i] = fmadd<T>(rv[i], rv[i], acc[i]);
+    }
+    st_lanes<T, L>(x + base, xv);
+    st_lanes<T, L>(r + base, rv);
+  }
+  double d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = double(acc[i]);
+  lane_reduce_commit<L>(d, a.red);
+}
+
+// K_P: p = r + b p
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads) k_cg_dir(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  T cb[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) cb[i] = T(a.red.c.cg_b[lane0 + i]);
+  const T* r = static_cast<const T*>(a.r);
+  T* p = static_cast<T*>(a.p);
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    T pv[L], rv[L];
+    ld_lanes<T, L>(p + base, pv);
+    ld_lanes<T, L>(r + base, rv);
+#pragma unroll
+    for (int i = 0; i < L; ++i) pv[i] = fmadd<T>(cb[i], pv[i], rv[i]);
+    st_lanes<T, L>(p + base, pv);
+  }
+}
+
+// v = x (FP64 mode) or v0 + d (mixed mode)
+template <typename T, int L, bool MIXED>
+__device__ __forceinline__ void load_v(const VecArgs& a, size_t base, double (&v)[L]) {
+  T xv[L];
+  ld_lanes<T, L>(static_cast<const T*>(a.x) + base, xv);
+#pragma unroll
+  for (int i = 0; i < L; ++i) v[i] = double(xv[i]);
+  if constexpr (MIXED) {
+    T dv[L];
+    ld_lanes<T, L>(static_cast<const T*>(a.x2) + base, dv);
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] += double(dv[i]);
+  }
+}
+
+// K_D: u.v
+template <typename T, int L, bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_dot_uv(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  double acc[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) acc[i] = 0.0;
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    double uv[L], v[L];
+    ld_lanes<double, L>(a.u + base, uv);
+    load_v<T, L, MIXED>(a, base, v);
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc[i] = fma(uv[i], v[i], acc[i]);
+  }
+  lane_reduce_commit<L>(acc, a.red);
+}
+
+// K_F: q = v / beta, Bq_new = u / beta, Bq_prev slot cleared for lanes that restart.
+template <typename T, int L, bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_finish(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const LaneCtl& c = a.red.c;
+  double ib[L];
+  bool keep[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int l = lane0 + i;
+    ib[i] = c.inv_beta[l];
+    keep[i] = (c.state[l] == LS_ACTIVE && c.n[l] >= 1 && ib[i] != 0.0);
+  }
+  const int slot = (*a.step) & 1;             // step already advanced by FIN_BETA
+  double* Bq_new = slot ? a.ring1 : a.ring0;
+  double* Bq_old = slot ? a.ring0 : a.ring1;
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    double uv[L], v[L], qn[L], bn[L];
+    ld_lanes<double, L>(a.u + base, uv);
+    load_v<T, L, MIXED>(a, base, v);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      qn[i] = (ib[i] != 0.0) ? v[i] * ib[i] : 0.0;
+      bn[i] = (ib[i] != 0.0) ? uv[i] * ib[i] : 0.0;
+    }
+    st_lanes<double, L>(a.q + base, qn);
+    st_lanes<double, L>(Bq_new + base, bn);
+    bool any_clear = false;
+#pragma unroll
+    for (int i = 0; i < L; ++i) any_clear |= !keep[i];
+    if (any_clear) {
+      double old[L];
+      ld_lanes<double, L>(Bq_old + base, old);
+#pragma unroll
+      for (int i = 0; i < L; ++i)
+        if (!keep[i]) old[i] = 0.0;
+      st_lanes<double, L>(Bq_old + base, old);
+    }
+  }
+}
+
+// ===========================================================================
+// K4: per-shift recurrences on the pattern rows of each lane's column
+// ===========================================================================
+struct ShiftArgs {
+  LaneCtl c;
+  Jobs jobs;
+  int W, S, Pmax, nsplit;
+  const double* eps;        // S: Re z_k
+  const double* zim;        // S: Im z_k (used when col_eta == 0)
+  int col_eta;              // 1: column c uses Re z_k + i*eta[c]
+  const int64_t* job_off;   // n_jobs + 1
+  const int32_t* prow;      // pattern rows (library order), job_off layout
+  double2* pbuf;            // [W][Pmax][S]
+  double2* xbuf;            // [W][Pmax][S]
+  double2* dg;              // [W][2][S][2]  (d, g) per step parity
+  const double* q;          // FP64 q_n (M x W)
+  double2* G;               // output, job_off layout x S
+  int32_t* out_iters;
+  int32_t* out_status;
+  double* out_resid;
+  double tol;
+  int max_iter;
+};
+
+__global__ void __launch_bounds__(kThreads) k_shift(const ShiftArgs a) {
+  const int lane = blockIdx.x;
+  const int split = blockIdx.y;
+  const LaneCtl& c = a.c;
+  if (c.state[lane] != LS_ACTIVE) return;
+  __shared__ double2 s_l[kMaxShifts];
+  __shared__ double2 s_z[kMaxShifts];
+  __shared__ double s_red[kThreads / 32];
+  __shared__ int s_bad;
+  const int S = a.S;
+  const int job = c.job[lane];
+  const int nprev = c.n[lane];
+  const int n = nprev + 1;                 // step processed now
+  const int brk = c.brk[lane];
+  const int64_t off = a.job_off[job];
+  const int P = (int)(a.job_off[job + 1] - off);
+  const double alpha = c.alpha[lane];
+  const double bp = c.beta_prev[lane];
+  const double b0 = c.beta0[lane];
+  const double unorm = c.unorm[lane];
+  const double eta = a.jobs.eta[job];
+  double2* dg = a.dg + (size_t)lane * 4 * S;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  double rmax = 0.0;
+  if (!brk) {
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+      const double2 sigma = make_double2(a.eps[k], a.col_eta ? eta : a.zim[k]);
+      double2 l, d, g;
+      if (n == 1) {
+        l = make_double2(0.0, 0.0);
+        d = make_double2(sigma.x - alpha, sigma.y);
+        g = make_double2(b0, 0.0);
+      } else {
+        const double2 dprev = dg[((nprev & 1) * S + k) * 2 + 0];
+        const double2 gprev = dg[((nprev & 1) * S + k) * 2 + 1];
+        l = cdiv(make_double2(-bp, 0.0), dprev);
+        d = make_double2(sigma.x - alpha + l.x * bp, sigma.y + l.y * bp);
+        g = cmul(make_double2(-l.x, -l.y), gprev);
+      }
+      const double2 zeta = cdiv(g, d);
+      if (split == 0) {
+        dg[((n & 1) * S + k) * 2 + 0] = d;
+        dg[((n & 1) * S + k) * 2 + 1] = g;
+      }
+      s_l[k] = l;
+      s_z[k] = zeta;
+      const double res = cabs2(zeta) * unorm;
+      if (!isfinite(res)) s_bad = 1;       // benign race: every writer stores 1
+      rmax = fmax(rmax, res);
+    }
+  }
+  // block max of the residual estimates
+  for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = rmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+    s_red[0] = m;
+  }
+  __syncthreads();
+  rmax = s_red[0];
+  const bool bad = brk || s_bad;
+  const bool conv = !bad && rmax <= a.tol;
+  const bool fin = bad || conv || n >= a.max_iter;
+  const int rows_per = (P + a.nsplit - 1) / a.nsplit;
+  const int i0 = split * rows_per;
+  const int i1 = min(P, i0 + rows_per);
+  double2* pb = a.pbuf + (size_t)lane * a.Pmax * S;
+  double2* xb = a.xbuf + (size_t)lane * a.Pmax * S;
+  double2* Gj = a.G + (size_t)off * S;
+  const int total = (i1 - i0) * S;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int i = i0 + t / S;
+    const int k = t - (t / S) * S;
+    const size_t e = (size_t)i * S + k;
+    double2 xv;
+    if (!bad) {
+      const double qi = a.q[(size_t)a.prow[off + i] * a.W + lane];
+      double2 pv;
+      if (n == 1) {
+        pv = make_double2(qi, 0.0);
+        xv = cmul(s_z[k], pv);
+      } else {
+        const double2 po = pb[e];
+        const double2 lp = cmul(s_l[k], po);
+        pv = make_double2(qi - lp.x, -lp.y);
+        xv = cadd(xb[e], cmul(s_z[k], pv));
+      }
+      pb[e] = pv;
+      xb[e] = xv;
+    } else {
+      xv = (nprev >= 1) ? xb[e] : make_double2(0.0, 0.0);
+    }
+    if (fin) Gj[e] = xv;
+  }
+  if (fin && split == 0 && threadIdx.x == 0) {
+    a.out_iters[job] = bad ? nprev : n;
+    a.out_status[job] = bad ? GSK_BREAKDOWN : (conv ? GSK_CONVERGED : GSK_NOT_CONVERGED);
+    a.out_resid[job] = bad ? (double)NAN : rmax;
+    c.done[lane] = 1;
+    c.cg_on[lane] = 0;
+  }
+}
+
+// ===========================================================================
+// Prime / wrap-up
+// ===========================================================================
+struct PrimeArgs {
+  LaneCtl c;
+  Jobs jobs;
+  GraphCtl gc;
+  int W;
+};
+
+__global__ void k_prime(const PrimeArgs a) {
+  const int l = threadIdx.x;
+  const LaneCtl& c = a.c;
+  if (l < a.W) {
+    if (l < a.jobs.n_jobs) {
+      c.job[l] = a.jobs.queue[l];
+      c.state[l] = LS_SEED;
+    } else {
+      c.job[l] = -1;
+      c.state[l] = LS_IDLE;
+    }
+    c.n[l] = 0;
+    c.done[l] = 0;
+    c.brk[l] = 0;
+    c.alpha[l] = 0.0;
+    c.beta_prev[l] = 0.0;
+    c.beta0[l] = 0.0;
+    c.inv_beta[l] = 0.0;
+    c.cg_on[l] = 0;
+    c.cg_a[l] = 0.0;
+    c.cg_b[l] = 0.0;
+  }
+  if (l == 0) {
+    *c.queue_head = min(a.W, a.jobs.n_jobs);
+    *c.step = 0;
+    *c.cg_iter = 0;
+    *c.cg_total = 0;
+    *c.red_counter = 0u;
+    *c.unfinished = a.jobs.n_jobs;
+    if (a.gc.use_graph) cudaGraphSetConditional(a.gc.h_outer, a.jobs.n_jobs > 0 ? 1u : 0u);
+  }
+}
+
+// Columns still running when the step cap stopped the loop: write their last
+// iterate with GSK_TIMEOUT; columns never started: zero G, GSK_TIMEOUT.
+struct WrapArgs {
+  LaneCtl c;
+  Jobs jobs;
+  int W, S, Pmax;
+  const int64_t* job_off;
+  const double2* xbuf;
+  double2* G;
+  int32_t* out_iters;
+  int32_t* out_status;
+  double* out_resid;
+};
+
+__global__ void k_wrapup(const WrapArgs a) {
+  const int lane = blockIdx.x;
+  if (lane < a.W) {
+    const LaneCtl& c = a.c;
+    if (c.state[lane] == LS_ACTIVE && !c.done[lane]) {
+      const int job = c.job[lane];
+      const int64_t off = a.job_off[job];
+      const int P = (int)(a.job_off[job + 1] - off);
+      const double2* xb = a.xbuf + (size_t)lane * a.Pmax * a.S;
+      const bool have_x = c.n[lane] >= 1;
+      for (int t = threadIdx.x; t < P * a.S; t += blockDim.x)
+        a.G[(size_t)off * a.S + t] = have_x ? xb[t] : make_double2(0.0, 0.0);
+      if (threadIdx.x == 0) {
+        a.out_iters[job] = c.n[lane];
+        a.out_status[job] = GSK_TIMEOUT;
+        a.out_resid[job] = (double)NAN;
+      }
+    }
+  }
+}
+
+__global__ void k_unstarted(Jobs jobs, const int64_t* job_off, int S, double2* G, int32_t* out_status,
+                            int32_t* out_iters, double* out_resid) {
+  for (int j = blockIdx.x; j < jobs.n_jobs; j += gridDim.x) {
+    if (out_status[j] >= 0) continue;
+    const int64_t off = job_off[j];
+    const int64_t cnt = (job_off[j + 1] - off) * S;
+    for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) G[off * S + t] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+      out_status[j] = GSK_TIMEOUT;
+      out_iters[j] = 0;
+      out_resid[j] = (double)NAN;
+    }
+  }
+}
+
+// ===========================================================================
+// Host orchestration
+// ===========================================================================
+namespace {
+
+#define GSK_CUDA_TRY(expr)                 \
+  do {                                     \
+    cudaError_t _e = (expr);               \
+    if (_e != cudaSuccess) return _e;      \
+  } while (0)
+
+struct GraphBuilder {
+  cudaGraph_t g;
+  cudaGraphNode_t last{};
+  bool has_last = false;
+  cudaError_t err = cudaSuccess;
+
+  explicit GraphBuilder(cudaGraph_t graph) : g(graph) {}
+
+  template <typename A>
+  void kernel(void (*f)(A), dim3 grid, dim3 block, const A& arg) {
+    if (err != cudaSuccess) return;
+    cudaKernelNodeParams p = {};
+    p.func = reinterpret_cast<void*>(f);
+    p.gridDim = grid;
+    p.blockDim = block;
+    p.sharedMemBytes = 0;
+    void* args[1] = {const_cast<A*>(&arg)};
+    p.kernelParams = args;
+    p.extra = nullptr;
+    cudaGraphNode_t n;
+    err = cudaGraphAddKernelNode(&n, g, has_last ? &last : nullptr, has_last ? 1 : 0, &p);
+    if (err == cudaSuccess) {
+      last = n;
+      has_last = true;
+    }
+  }
+
+  // Appends a WHILE node driven by handle h; returns its body graph.
+  cudaGraph_t while_node(cudaGraphConditionalHandle h) {
+    if (err != cudaSuccess) return nullptr;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n;
+    err = cudaGraphAddNode(&n, g, has_last ? &last : nullptr, nullptr, has_last ? 1 : 0, &cp);
+    if (err != cudaSuccess) return nullptr;
+    last = n;
+    has_last = true;
+    return cp.conditional.phGraph_out[0];
+  }
+};
+
+// Everything one solve launches, with the launch shapes.
+struct Plan {
+  int W = 64;
+  int L = 2;
+  bool mixed = false;
+  bool refine = true;
+  int grid_rows = 1;     // SpMM CTAs (== lay.n_ctas)
+  int grid_vec = 1;      // vector-kernel CTAs
+  int nsplit = 1;
+  // kernel argument blocks
+  SpmmArgs<double, double, double> spA;
+  SpmmArgs<double, double, double> spB64;
+  SpmmArgs<float, float, float> spB32[2];
+  SpmmArgs<double, float, float> spR;
+  VecArgs upd, cgu[2], cgp[2], dot, fin;
+  ShiftArgs sh;
+  PrimeArgs prime;
+  WrapArgs wrap;
+};
+
+template <int L>
+struct Kernels {
+  // FP64 mode
+  static constexpr auto spmm64 = k_spmm<double, double, double, double, L, SP_DOT>;
+  static constexpr auto upd64 = k_update<double, L>;
+  static constexpr auto cgu64 = k_cg_update<double, L>;
+  static constexpr auto cgp64 = k_cg_dir<double, L>;
+  static constexpr auto dot64 = k_dot_uv<double, L, false>;
+  static constexpr auto fin64 = k_finish<double, L, false>;
+  // mixed mode
+  static constexpr auto spmm32 = k_spmm<float, float, float, float, L, SP_DOT>;
+  static constexpr auto resid = k_spmm<double, float, float, double, L, SP_RESID>;
+  static constexpr auto upd32 = k_update<float, L>;
+  static constexpr auto cgu32 = k_cg_update<float, L>;
+  static constexpr auto cgp32 = k_cg_dir<float, L>;
+  static constexpr auto dotm = k_dot_uv<float, L, true>;
+  static constexpr auto finm = k_finish<float, L, true>;
+};
+
+// Launch of one kernel either into a graph (builder) or onto a stream.
+struct Launcher {
+  GraphBuilder* gb = nullptr;
+  cudaStream_t stream = nullptr;
+  template <typename A>
+  cudaError_t operator()(void (*f)(A), dim3 grid, dim3 block, const A& arg) {
+    if (gb) {
+      gb->kernel(f, grid, block, arg);
+      return gb->err;
+    }
+    f<<<grid, block, 0, stream>>>(arg);
+    return cudaGetLastError();
+  }
+};
+
+template <int L>
+cudaError_t launch_cg_iteration(const Plan& P, Launcher& la, int pass) {
+  using K = Kernels<L>;
+  const dim3 blk(kThreads);
+  if (!P.mixed) {
+    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spB64));
+    GSK_CUDA_TRY(la(K::cgu64, dim3(P.grid_vec), blk, P.cgu[0]));
+    GSK_CUDA_TRY(la(K::cgp64, dim3(P.grid_vec), blk, P.cgp[0]));
+  } else {
+    GSK_CUDA_TRY(la(K::spmm32, dim3(P.grid_rows), blk, P.spB32[pass]));
+    GSK_CUDA_TRY(la(K::cgu32, dim3(P.grid_vec), blk, P.cgu[pass]));
+    GSK_CUDA_TRY(la(K::cgp32, dim3(P.grid_vec), blk, P.cgp[pass]));
+  }
+  return cudaSuccess;
+}
+
+template <int L>
+cudaError_t launch_step_head(const Plan& P, Launcher& la) {
+  using K = Kernels<L>;
+  const dim3 blk(kThreads);
+  GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spA));
+  if (!P.mixed)
+    GSK_CUDA_TRY(la(K::upd64, dim3(P.grid_vec), blk, P.upd));
+  else
+    GSK_CUDA_TRY(la(K::upd32, dim3(P.grid_vec), blk, P.upd));
+  GSK_CUDA_TRY(la(k_shift, dim3(P.W, P.nsplit), blk, P.sh));
+  return cudaSuccess;
+}
+
+template <int L>
+cudaError_t launch_step_tail(const Plan& P, Launcher& la) {
+  using K = Kernels<L>;
+  const dim3 blk(kThreads);
+  if (!P.mixed) {
+    GSK_CUDA_TRY(la(K::dot64, dim3(P.grid_vec), blk, P.dot));
+    GSK_CUDA_TRY(la(K::fin64, dim3(P.grid_vec), blk, P.fin));
+  } else {
+    GSK_CUDA_TRY(la(K::dotm, dim3(P.grid_vec), blk, P.dot));
+    GSK_CUDA_TRY(la(K::finm, dim3(P.grid_vec), blk, P.fin));
+  }
+  return cudaSuccess;
+}
+
+template <int L>
+cudaError_t launch_resid(const Plan& P, Launcher& la) {
+  using K = Kernels<L>;
+  return la(K::resid, dim3(P.grid_rows), dim3(kThreads), P.spR);
+}
+
+// Builds the whole solve as one graph: prime -> WHILE(outer) { head, WHILE(cg1),
+// [resid, WHILE(cg2)], tail } -> wrap-up.
+template <int L>
+cudaError_t build_graph(Plan& P, cudaGraphExec_t* exec) {
+  cudaGraph_t top;
+  GSK_CUDA_TRY(cudaGraphCreate(&top, 0));
+  cudaError_t err = cudaSuccess;
+  do {
+    cudaGraphConditionalHandle h_outer, h_in1, h_in2 = 0;
+    err = cudaGraphConditionalHandleCreate(&h_outer, top, 0, 0);
+    if (err) break;
+    GraphBuilder gtop(top);
+    // handles of the inner loops live in the outer body graph: created after it exists
+    GraphCtl gc{};
+    gc.use_graph = 1;
+    gc.h_outer = h_outer;
+    gc.max_inner = P.upd.red.gc.max_inner;
+    gc.step_cap = P.upd.red.gc.step_cap;
+    P.prime.gc = gc;
+    Launcher lt{&gtop, nullptr};
+    err = lt(k_prime, dim3(1), dim3(kMaxW), P.prime);
+    if (err) break;
+    cudaGraph_t body = gtop.while_node(h_outer);
+    if ((err = gtop.err)) break;
+    err = cudaGraphConditionalHandleCreate(&h_in1, body, 0, 0);
+    if (err) break;
+    if (P.mixed && P.refine) {
+      err = cudaGraphConditionalHandleCreate(&h_in2, body, 0, 0);
+      if (err) break;
+    }
+    gc.h_inner1 = h_in1;
+    gc.h_inner2 = h_in2;
+    // propagate graph control into every argument block
+    RedArgs* reds[] = {&P.spA.red, &P.spB64.red, &P.spB32[0].red, &P.spB32[1].red, &P.spR.red,
+                       &P.upd.red, &P.cgu[0].red, &P.cgu[1].red, &P.cgp[0].red, &P.cgp[1].red,
+                       &P.dot.red, &P.fin.red};
+    for (RedArgs* r : reds) r->gc = gc;
+    GraphBuilder gb(body);
+    Launcher lb{&gb, nullptr};
+    err = launch_step_head<L>(P, lb);
+    if (err) break;
+    cudaGraph_t in1 = gb.while_node(h_in1);
+    if ((err = gb.err)) break;
+    {
+      GraphBuilder gi(in1);
+      Launcher li{&gi, nullptr};
+      err = launch_cg_iteration<L>(P, li, 0);
+      if (err) break;
+    }
+    if (P.mixed && P.refine) {
+      err = launch_resid<L>(P, lb);
+      if (err) break;
+      cudaGraph_t in2 = gb.while_node(h_in2);
+      if ((err = gb.err)) break;
+      GraphBuilder gi(in2);
+      Launcher li{&gi, nullptr};
+      err = launch_cg_iteration<L>(P, li, 1);
+      if (err) break;
+    }
+    err = launch_step_tail<L>(P, lb);
+    if (err) break;
+    err = lt(k_wrapup, dim3(P.W), dim3(kThreads), P.wrap);
+    if (err) break;
+    err = cudaGraphInstantiate(exec, top, 0);
+  } while (0);
+  cudaGraphDestroy(top);
+  return err;
+}
+
+// Host-driven loop with the same kernels (no graph): reads the loop flags back.
+template <int L>
+cudaError_t run_host_loop(Plan& P, cudaStream_t s, int* h_flag, const int* d_unfinished) {
+  Launcher la{nullptr, s};
+  GSK_CUDA_TRY(la(k_prime, dim3(1), dim3(kMaxW), P.prime));
+  auto flag = [&](int* out) -> cudaError_t {
+    GSK_CUDA_TRY(cudaMemcpyAsync(out, d_unfinished, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return cudaStreamSynchronize(s);
+  };
+  const int max_inner = P.upd.red.gc.max_inner;
+  for (int step = 0; step < P.upd.red.gc.step_cap; ++step) {
+    GSK_CUDA_TRY(launch_step_head<L>(P, la));
+    // the update kernel leaves the number of lanes needing CG in *unfinished
+    GSK_CUDA_TRY(flag(h_flag));
+    for (int it = 0; it < max_inner && *h_flag > 0; ++it) {
+      GSK_CUDA_TRY(launch_cg_iteration<L>(P, la, 0));
+      GSK_CUDA_TRY(flag(h_flag));
+    }
+    if (P.mixed && P.refine) {
+      GSK_CUDA_TRY(launch_resid<L>(P, la));
+      GSK_CUDA_TRY(flag(h_flag));
+      for (int it = 0; it < max_inner && *h_flag > 0; ++it) {
+        GSK_CUDA_TRY(launch_cg_iteration<L>(P, la, 1));
+        GSK_CUDA_TRY(flag(h_flag));
+      }
+    }
+    GSK_CUDA_TRY(launch_step_tail<L>(P, la));
+    GSK_CUDA_TRY(flag(h_flag));
+    if (*h_flag == 0) break;
+  }
+  return la(k_wrapup, dim3(P.W), dim3(kThreads), P.wrap);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+// ===========================================================================
+// gsk_solve
+// ===========================================================================
+int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols,
+               const int32_t* cols, const gsk_options* opt_in, double* G_out, int32_t* iters,
+               int32_t* status, double* resid) {
+  gsk_options opt;
+  gsk_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (S < 1 || S > kMaxShifts || n_cols < 0 || !z || (n_cols > 0 && (!cols || !G_out)))
+    return GSK_EINVAL;
+  if (opt.precision != GSK_FP64 && opt.precision != GSK_MIXED) return GSK_EINVAL;
+  if (!(opt.tol > 0.0) || opt.max_iter < 1) return GSK_EINVAL;
+  if (opt.batch_w != 0 && opt.batch_w != 32 && opt.batch_w != 64 && opt.batch_w != 128) return GSK_EINVAL;
+  if (opt.precision == GSK_FP64 && opt.batch_w == 128) return GSK_ENOTSUP;
+  if (opt.max_inner < 1) opt.max_inner = 200;
+  for (int k = 0; k < S; ++k)
+    if (!isfinite(z[2 * k]) || !isfinite(z[2 * k + 1])) return GSK_EINVAL;
+  if (!eta)
+    for (int k = 0; k < S; ++k)
+      if (!(z[2 * k + 1] > 0.0)) return GSK_EINVAL;
+  if (n_cols == 0) return GSK_OK;
+  const int M = h->M;
+  {
+    std::vector<char> seen(M, 0);
+    for (int c = 0; c < n_cols; ++c) {
+      if (cols[c] < 0 || cols[c] >= M || seen[cols[c]]) return GSK_EINVAL;
+      seen[cols[c]] = 1;
+      if (eta && !(eta[c] > 0.0 && isfinite(eta[c]))) return GSK_EINVAL;
+    }
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
+  cudaStream_t stream = static_cast<cudaStream_t>(opt.stream);
+
+  Plan P;
+  P.mixed = (opt.precision == GSK_MIXED);
+  P.refine = P.mixed && opt.refine != 0;
+  int W = opt.batch_w;
+  if (W == 0) {
+    // lanes in flight: enough columns to fill the batch, favouring wide batches
+    W = (n_cols > 64 && P.mixed) ? 128 : 64;
+    if (n_cols <= 32) W = 32;
+    if (!P.mixed && W > 64) W = 64;
+  }
+  P.W = W;
+  P.L = W / 32;
+  P.grid_rows = h->lay.n_ctas;
+  P.grid_vec = std::max(1, std::min((M + kWarps - 1) / kWarps, h->num_sms * 6));
+
+  // ---- job arrays (host) ----
+  std::vector<int64_t> job_off(n_cols + 1, 0);
+  for (int c = 0; c < n_cols; ++c) {
+    const int j = cols[c];
+    job_off[c + 1] = job_off[c] + (h->row_ptr[j + 1] - h->row_ptr[j]);
+  }
+  const int64_t n_elem = job_off[n_cols];
+  int Pmax = 0;
+  for (int c = 0; c < n_cols; ++c) Pmax = std::max<int>(Pmax, (int)(job_off[c + 1] - job_off[c]));
+  std::vector<int32_t> prow(n_elem), col_row(n_cols), queue(n_cols);
+  std::vector<double> jeta(n_cols);
+  for (int c = 0; c < n_cols; ++c) {
+    const int j = cols[c];
+    col_row[c] = h->row_lib[j];
+    jeta[c] = eta ? eta[c] : 0.0;
+    int64_t t = job_off[c];
+    for (int64_t e = h->row_ptr[j]; e < h->row_ptr[j + 1]; ++e) prow[t++] = h->row_lib[h->col_idx[e]];
+    queue[c] = c;
+  }
+  std::vector<double> eps(2 * S);
+  for (int k = 0; k < S; ++k) {
+    eps[k] = z[2 * k];
+    eps[S + k] = z[2 * k + 1];
+  }
+
+  // ---- device workspace ----
+  const size_t MW = (size_t)M * W;
+  const size_t b64 = align_up(MW * sizeof(double), 256);
+  const size_t b32 = align_up(MW * sizeof(float), 256);
+  const size_t bcg = P.mixed ? b32 : b64;
+  const size_t vec_bytes = 4 * b64 + 5 * bcg;
+  if (h->ws_vec.ensure(vec_bytes) != cudaSuccess) return GSK_ENOMEM;
+  char* vb = h->ws_vec.as<char>();
+  double* q = reinterpret_cast<double*>(vb);
+  double* ring0 = reinterpret_cast<double*>(vb + b64);
+  double* ring1 = reinterpret_cast<double*>(vb + 2 * b64);
+  double* u = reinterpret_cast<double*>(vb + 3 * b64);
+  char* cgb = vb + 4 * b64;
+  void* x = cgb;
+  void* x2 = cgb + bcg;
+  void* r = cgb + 2 * bcg;
+  void* p = cgb + 3 * bcg;
+  void* Bp = cgb + 4 * bcg;
+
+  // lane control block
+  const int n_red = std::max(P.grid_rows, P.grid_vec);
+  const size_t lane_bytes = 64 * kMaxW * sizeof(double) + (size_t)n_red * kMaxW * sizeof(double) + 256;
+  if (h->ws_lane.ensure(lane_bytes) != cudaSuccess) return GSK_ENOMEM;
+  char* lb = h->ws_lane.as<char>();
+  LaneCtl c{};
+  {
+    size_t o = 0;
+    auto take_i = [&]() { int* ptr = reinterpret_cast<int*>(lb + o); o += kMaxW * sizeof(double); return ptr; };
+    auto take_d = [&]() { double* ptr = reinterpret_cast<double*>(lb + o); o += kMaxW * sizeof(double); return ptr; };
+    c.job = take_i(); c.state = take_i(); c.n = take_i(); c.done = take_i(); c.brk = take_i();
+    c.alpha = take_d(); c.beta_prev = take_d(); c.beta0 = take_d(); c.unorm = take_d();
+    c.inv_beta = take_d(); c.rr = take_d(); c.rr_target = take_d(); c.cg_a = take_d();
+    c.cg_b = take_d(); c.cg_on = take_i(); c.red_out = take_d();
+    int* scal = take_i();
+    c.queue_head = scal + 0; c.cg_iter = scal + 1; c.step = scal + 2; c.unfinished = scal + 3;
+    c.cg_total = scal + 4;
+    c.red_counter = reinterpret_cast<unsigned int*>(scal + 5);
+    c.partials = reinterpret_cast<double*>(lb + o);
+  }
+
+  // job arrays
+  const size_t jb_bytes = align_up((n_cols + 1) * sizeof(int64_t), 256) +
+                          align_up(n_elem * sizeof(int32_t), 256) +
+                          3 * align_up(n_cols * sizeof(int32_t), 256) +
+                          align_up(n_cols * sizeof(double), 256) * 2 +
+                          align_up(2 * S * sizeof(double), 256) +
+                          align_up(n_cols * sizeof(int32_t), 256);
+  if (h->ws_jobs.ensure(jb_bytes) != cudaSuccess) return GSK_ENOMEM;
+  char* jbp = h->ws_jobs.as<char>();
+  size_t jo = 0;
+  auto jtake = [&](size_t bytes) { void* ptr = jbp + jo; jo += align_up(bytes, 256); return ptr; };
+  int64_t* d_job_off = static_cast<int64_t*>(jtake((n_cols + 1) * sizeof(int64_t)));
+  int32_t* d_prow = static_cast<int32_t*>(jtake(n_elem * sizeof(int32_t)));
+  int32_t* d_col_row = static_cast<int32_t*>(jtake(n_cols * sizeof(int32_t)));
+  int32_t* d_queue = static_cast<int32_t*>(jtake(n_cols * sizeof(int32_t)));
+  int32_t* d_status = static_cast<int32_t*>(jtake(n_cols * sizeof(int32_t)));
+  double* d_eta = static_cast<double*>(jtake(n_cols * sizeof(double)));
+  double* d_resid = static_cast<double*>(jtake(n_cols * sizeof(double)));
+  double* d_eps = static_cast<double*>(jtake(2 * S * sizeof(double)));
+  int32_t* d_iters = static_cast<int32_t*>(jtake(n_cols * sizeof(int32_t)));
+
+  // shift state
+  const size_t sh_bytes = 2 * align_up((size_t)W * Pmax * S * sizeof(double2), 256) +
+                          align_up((size_t)W * 4 * S * sizeof(double2), 256);
+  if (h->ws_shift.ensure(sh_bytes) != cudaSuccess) return GSK_ENOMEM;
+  double2* pbuf = h->ws_shift.as<double2>();
+  double2* xbuf = reinterpret_cast<double2*>(h->ws_shift.as<char>() + align_up((size_t)W * Pmax * S * sizeof(double2), 256));
+  double2* dgb = reinterpret_cast<double2*>(h->ws_shift.as<char>() + 2 * align_up((size_t)W * Pmax * S * sizeof(double2), 256));
+
+  // output staging for host G buffers
+  cudaPointerAttributes pa{};
+  bool g_on_device = false;
+  if (cudaPointerGetAttributes(&pa, G_out) == cudaSuccess)
+    g_on_device = (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  double2* Gd = reinterpret_cast<double2*>(G_out);
+  const size_t g_bytes = (size_t)n_elem * S * sizeof(double2);
+  if (!g_on_device) {
+    if (h->ws_gstage.ensure(g_bytes) != cudaSuccess) return GSK_ENOMEM;
+    Gd = h->ws_gstage.as<double2>();
+  }
+
+  // uploads
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+  };
+  up(d_job_off, job_off.data(), (n_cols + 1) * sizeof(int64_t));
+  up(d_prow, prow.data(), n_elem * sizeof(int32_t));
+  up(d_col_row, col_row.data(), n_cols * sizeof(int32_t));
+  up(d_queue, queue.data(), n_cols * sizeof(int32_t));
+  up(d_eta, jeta.data(), n_cols * sizeof(double));
+  up(d_eps, eps.data(), 2 * S * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0xff, n_cols * sizeof(int32_t), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vb, 0, vec_bytes, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lb, 0, lane_bytes, stream);
+  if (e != cudaSuccess) return GSK_ECUDA;
+
+  // ---- argument blocks ----
+  Jobs jobs{n_cols, d_queue, d_col_row, d_eta};
+  GraphCtl gc{};
+  gc.use_graph = 0;
+  gc.max_inner = opt.max_inner;
+  const int per_lane = (n_cols + W - 1) / W + 1;
+  gc.step_cap = (int)std::min<int64_t>((int64_t)(opt.max_iter + 2) * per_lane, 2000000000LL);
+  const double itol = (opt.inner_tol > 0.0) ? opt.inner_tol : (P.mixed ? 1e-6 : 1e-12);
+  RedArgs rb{};
+  rb.c = c;
+  rb.jobs = jobs;
+  rb.gc = gc;
+  rb.W = W;
+  rb.inner_tol2 = itol * itol;
+  rb.max_iter = opt.max_iter;
+  auto red = [&](int fin) { RedArgs x = rb; x.fin = fin; return x; };
+
+  const Layout& g = h->lay;
+  P.spA = {g, h->d_A64.as<double>(), q, u, nullptr, nullptr, nullptr, red(FIN_ALPHA)};
+  P.spB64 = {g, h->d_B64.as<double>(), static_cast<double*>(p), static_cast<double*>(Bp), nullptr, nullptr, nullptr, red(FIN_CG_A)};
+  for (int ps = 0; ps < 2; ++ps)
+    P.spB32[ps] = {g, h->d_B32.as<float>(), static_cast<float*>(p), static_cast<float*>(Bp), nullptr, nullptr, nullptr, red(FIN_CG_A)};
+  P.spR = {g, h->d_B64.as<double>(), static_cast<float*>(x), static_cast<float*>(r), u, static_cast<float*>(p), static_cast<float*>(x2), red(FIN_RESID)};
+  VecArgs va{};
+  va.M = M; va.q = q; va.ring0 = ring0; va.ring1 = ring1; va.u = u;
+  va.r = r; va.p = p; va.Bp = Bp; va.x = x; va.x2 = x2; va.step = c.step;
+  P.upd = va; P.upd.red = red(FIN_UNORM);
+  for (int ps = 0; ps < 2; ++ps) {
+    P.cgu[ps] = va;
+    P.cgu[ps].x = ps == 0 ? x : x2;
+    P.cgu[ps].red = red(FIN_CG_RR);
+    P.cgu[ps].red.max_iter = ps == 0 ? opt.max_iter : -1;
+    P.cgp[ps] = va;
+    P.cgp[ps].red = red(FIN_SUM);
+  }
+  P.dot = va; P.dot.red = red(FIN_BETA);
+  P.fin = va; P.fin.red = red(FIN_SUM);
+  P.nsplit = std::max(1, std::min(8, (h->num_sms * 2) / W));
+  P.sh = ShiftArgs{c, jobs, W, S, Pmax, P.nsplit, d_eps, d_eps + S, eta ? 1 : 0, d_job_off, d_prow, pbuf, xbuf, dgb, q, Gd,
+                   d_iters, d_status, d_resid, opt.tol, opt.max_iter};
+  P.prime = PrimeArgs{c, jobs, gc, W};
+  P.wrap = WrapArgs{c, jobs, W, S, Pmax, d_job_off, xbuf, Gd, d_iters, d_status, d_resid};
+
+  // ---- run ----
+  auto run = [&](auto Ltag) -> cudaError_t {
+    constexpr int LL = decltype(Ltag)::value;
+    if (opt.use_graph) {
+      cudaGraphExec_t ex = nullptr;
+      cudaError_t ge = build_graph<LL>(P, &ex);
+      if (ge == cudaSuccess) {
+        ge = cudaGraphLaunch(ex, stream);
+        cudaGraphExecDestroy(ex);
+        return ge;
+      }
+      cudaGetLastError();
+      return ge;
+    }
+    int* hflag = nullptr;
+    GSK_CUDA_TRY(cudaMallocHost(&hflag, sizeof(int)));
+    cudaError_t he = run_host_loop<LL>(P, stream, hflag, c.unfinished);
+    cudaFreeHost(hflag);
+    return he;
+  };
+  if (P.L == 1)
+    e = run(std::integral_constant<int, 1>{});
+  else if (P.L == 2)
+    e = run(std::integral_constant<int, 2>{});
+  else
+    e = run(std::integral_constant<int, 4>{});
+  if (e != cudaSuccess) return GSK_ECUDA;
+  k_unstarted<<<std::min(n_cols, 1024), 128, 0, stream>>>(jobs, d_job_off, S, Gd, d_status, d_iters, d_resid);
+  if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
+
+  // ---- results ----
+  if (!g_on_device) e = cudaMemcpyAsync(G_out, Gd, g_bytes, cudaMemcpyDeviceToHost, stream);
+  std::vector<int32_t> h_it(n_cols), h_st(n_cols);
+  std::vector<double> h_rs(n_cols);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_it.data(), d_iters, n_cols * sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_st.data(), d_status, n_cols * sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_rs.data(), d_resid, n_cols * sizeof(double), cudaMemcpyDeviceToHost, stream);
+  int h_cnt[5] = {0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, c.queue_head, 5 * sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return GSK_ECUDA;
+  {
+    // scal layout: queue_head, cg_iter, step, unfinished, cg_total
+    const int64_t steps = h_cnt[2], cgt = h_cnt[4];
+    h->last.outer_steps = steps;
+    h->last.cg_iterations = cgt;
+    const int64_t per_step = 3 + 2 + ((P.mixed && P.refine) ? 1 : 0);
+    h->last.kernel_launches = 3 + steps * per_step + cgt * 3;
+    h->last.batch_w = W;
+    h->last.used_graph = opt.use_graph ? 1 : 0;
+  }
+  if (iters) memcpy(iters, h_it.data(), n_cols * sizeof(int32_t));
+  if (status) memcpy(status, h_st.data(), n_cols * sizeof(int32_t));
+  if (resid) memcpy(resid, h_rs.data(), n_cols * sizeof(double));
+  return GSK_OK;
+}
+
+}  // namespace gsk

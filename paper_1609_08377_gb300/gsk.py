@@ -1,0 +1,207 @@
+"""Thin Python binding of libgsk (argument marshalling only).
+
+Every computation happens in the CUDA library behind the C ABI declared in
+include/gsk.h; this module converts Python/NumPy/PyTorch arguments to plain
+pointers and sizes. Importing it loads libgsk.so and fails loudly when the
+library has not been built (there is no fallback path).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgsk.so")
+
+GSK_OK, GSK_EINVAL, GSK_ENOTSPD, GSK_ENOMEM, GSK_ECUDA, GSK_ETIMEOUT, GSK_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+GSK_CONVERGED, GSK_NOT_CONVERGED, GSK_BREAKDOWN, GSK_TIMEOUT = 0, 1, 2, 3
+GSK_FP64, GSK_MIXED = 0, 1
+GSK_SCHED_FIFO, GSK_SCHED_LEARNED = 0, 1
+
+
+class GskError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {code} ({strerror(code)})")
+        self.code = code
+
+
+class Stats(C.Structure):
+    _fields_ = [("outer_steps", C.c_int64), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64),
+                ("batch_w", C.c_int32), ("used_graph", C.c_int32)]
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class _Orbmap(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("orb_offset", C.c_void_p), ("orb_count", C.c_void_p), ("pos", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("batch_w", C.c_int32), ("refine", C.c_int32), ("sched", C.c_int32),
+                ("inner_tol", C.c_double), ("max_inner", C.c_int32), ("use_graph", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgsk.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "gsk_default_options": (None, [P]),
+        "gsk_create": (C.c_int, [P, P, P, P]),
+        "gsk_destroy": (C.c_int, [P]),
+        "gsk_dims": (C.c_int, [P, P, P]),
+        "gsk_pattern_offsets": (C.c_int, [P, I32, P, P]),
+        "gsk_solve": (C.c_int, [P, I32, P, P, I32, P, P, P, P, P, P]),
+        "gsk_density": (C.c_int, [P, I64, I32, P, P, D, D, P, P, P]),
+        "gsk_trace": (C.c_int, [P, I32, P, P, I32, P]),
+        "gsk_strerror": (C.c_char_p, [C.c_int]),
+        "gsk_last_stats": (C.c_int, [P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> C.CDLL:
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return _lib.gsk_strerror(int(code)).decode()
+
+
+def _check(code: int, where: str) -> None:
+    if code != GSK_OK:
+        raise GskError(code, where)
+
+
+def _ptr(a) -> int:
+    """Raw address of a NumPy array or a PyTorch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    _lib.gsk_default_options(C.byref(o))
+    names = {"precision": {"fp64": GSK_FP64, "mixed": GSK_MIXED},
+             "sched": {"fifo": GSK_SCHED_FIFO, "learned": GSK_SCHED_LEARNED}}
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k in names and isinstance(v, str):
+            v = names[k][v]
+        if k == "stream":
+            v = getattr(v, "cuda_stream", v)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One libgsk handle: the pencil (A, B) and its orbital-block map."""
+
+    def __init__(self, A, B, orb_offset, orb_count, pos=None):
+        self._keep = []
+        A = A.tocsr()
+        B = B.tocsr()
+        self._A = self._csr(A)
+        self._B = self._csr(B)
+        off = np.ascontiguousarray(orb_offset, dtype=np.int32)
+        cnt = np.ascontiguousarray(orb_count, dtype=np.int8)
+        ps = None if pos is None else np.ascontiguousarray(pos, dtype=np.float64)
+        self._keep += [off, cnt, ps]
+        om = _Orbmap(off.size, _ptr(off), _ptr(cnt), _ptr(ps))
+        h = C.c_void_p()
+        _check(_lib.gsk_create(C.byref(self._A), C.byref(self._B), C.byref(om), C.byref(h)), "gsk_create")
+        self._h = h
+        self._keep = []
+        m = C.c_int32()
+        nnz = C.c_int64()
+        _check(_lib.gsk_dims(self._h, C.byref(m), C.byref(nnz)), "gsk_dims")
+        self.M, self.nnz = int(m.value), int(nnz.value)
+
+    def _csr(self, X) -> _Csr:
+        rp = np.ascontiguousarray(X.indptr, dtype=np.int64)
+        ci = np.ascontiguousarray(X.indices, dtype=np.int32)
+        v = np.ascontiguousarray(X.data, dtype=np.float64)
+        self._keep += [rp, ci, v]
+        return _Csr(X.shape[0], _ptr(rp), _ptr(ci), _ptr(v))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.gsk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_stats(self) -> dict:
+        st = Stats()
+        _check(_lib.gsk_last_stats(self._h, C.byref(st)), "gsk_last_stats")
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def pattern_offsets(self, cols) -> np.ndarray:
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        out = np.empty(cols.size + 1, dtype=np.int64)
+        _check(_lib.gsk_pattern_offsets(self._h, cols.size, _ptr(cols), _ptr(out)), "gsk_pattern_offsets")
+        return out
+
+    def solve(self, z, cols, G, eta=None, options: Options | None = None, **kw):
+        """Run gsk_solve. G: device tensor or host array of offsets[-1]*S complex128.
+
+        Returns (iters, status, resid) as NumPy arrays.
+        """
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+        zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).ravel())
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        opt = options if options is not None else default_options(**kw)
+        n = cols.size
+        iters = np.empty(n, dtype=np.int32)
+        status = np.empty(n, dtype=np.int32)
+        resid = np.empty(n, dtype=np.float64)
+        rc = _lib.gsk_solve(self._h, z.size, _ptr(zz), _ptr(e), n, _ptr(cols), C.byref(opt), _ptr(G),
+                            _ptr(iters), _ptr(status), _ptr(resid))
+        _check(rc, "gsk_solve")
+        return iters, status, resid
+
+    def density(self, G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=None) -> None:
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        s = getattr(stream, "cuda_stream", stream)
+        _check(_lib.gsk_density(self._h, int(n_elem), eps.size, _ptr(eps), _ptr(w), float(mu), float(kT),
+                                _ptr(G), _ptr(rho), s), "gsk_density")
+
+    def trace(self, cols, rho, which: int) -> float:
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        out = C.c_double()
+        _check(_lib.gsk_trace(self._h, cols.size, _ptr(cols), _ptr(rho), int(which), C.byref(out)), "gsk_trace")
+        return float(out.value)
+
+
+def from_system(sys_, pos=True) -> Solver:
+    """Solver for a synthetic System (see synthetic.make_system)."""
+    return Solver(sys_.A, sys_.B, sys_.orb_offset, sys_.orb_count, sys_.pos if pos else None)
