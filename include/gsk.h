@@ -160,6 +160,21 @@ int gsk_density(gsk_handle h, int64_t n_elem, int32_t n_shifts, const double* ep
 int gsk_trace(gsk_handle h, int32_t n_cols, const int32_t* cols, const double* rho,
               int32_t which, double* out);
 
+/* Library row order: row_lib[i] = row of caller row i in the layout used by
+ * gsk_spmm (host array of M entries). */
+int gsk_row_order(gsk_handle h, int32_t* row_lib);
+
+/* n_rep applications of the solver's block SpMM kernel, Y = S X with S = A
+ * (which = 0) or B (which = 1), on W lanes (32, 64 or 128; 128 only for
+ * FP32): the same kernel, launch shape and epilogue (per-lane dot X.Y, kept
+ * internally) that gsk_solve runs, for timing and for callers working in the
+ * library's row order.
+ *   precision GSK_FP64: X, Y are double; GSK_MIXED: X, Y are float
+ *   X, Y      device, M x W row-major (lane fastest), rows in library order
+ *   stream    cudaStream_t or NULL. Asynchronous on that stream. */
+int gsk_spmm(gsk_handle h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y,
+             int32_t n_rep, void* stream);
+
 /* Counters of the last gsk_solve on this handle. */
 typedef struct {
   int64_t outer_steps;       /* Lanczos steps of the lane batch (lock-step) */

@@ -95,8 +95,12 @@ class LanczosResult:
 
 def lanczos_column(A, B, j: int, z, tol: float = 1e-8, max_iter: int = 5000,
                    check_every: int = 10, bsolve_tol: float = 1e-14,
-                   keep_full: bool = False) -> LanczosResult:
-    """O3 for one column j and all shifts z (eta may differ per shift)."""
+                   keep_full: bool = False, milestones=()) -> LanczosResult:
+    """O3 for one column j and all shifts z (eta may differ per shift).
+
+    milestones: residual levels above tol; the result's `reached` maps each to
+    the first checked step whose largest residual estimate was at or below it.
+    """
     z = np.asarray(z, dtype=np.complex128)
     M = A.shape[0]
     rows = pattern_rows(A, j)
@@ -113,6 +117,7 @@ def lanczos_column(A, B, j: int, z, tol: float = 1e-8, max_iter: int = 5000,
     resid = np.full(z.size, np.inf)
     n = 0
     converged = False
+    reached = {}
     while n < max_iter:
         n += 1
         w = A @ q
@@ -128,6 +133,9 @@ def lanczos_column(A, B, j: int, z, tol: float = 1e-8, max_iter: int = 5000,
             b = np.asarray(betas)
             y_all = np.stack([_tridiag_solve(a, b, beta0, zk) for zk in z], axis=1)
             resid = np.abs(y_all[-1, :]) * unorm
+            for m in milestones:
+                if m not in reached and resid.max() <= m:
+                    reached[m] = n
             if np.all(resid <= tol):
                 converged = True
                 break
@@ -145,7 +153,9 @@ def lanczos_column(A, B, j: int, z, tol: float = 1e-8, max_iter: int = 5000,
     x_full = None
     if keep_full:
         x_full = np.stack(Qfull, axis=1) @ y_all
-    return LanczosResult(G, n, resid, converged, np.asarray(alphas), np.asarray(betas), beta0, x_full)
+    res = LanczosResult(G, n, resid, converged, np.asarray(alphas), np.asarray(betas), beta0, x_full)
+    res.reached = reached
+    return res
 
 
 def lanczos_columns(A, B, cols, z_per_col, tol=1e-8, max_iter=5000, check_every=10,

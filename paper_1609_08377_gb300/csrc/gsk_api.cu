@@ -395,6 +395,18 @@ int gsk_destroy(gsk_handle h) {
   return GSK_OK;
 }
 
+int gsk_row_order(gsk_handle h, int32_t* row_lib) {
+  if (!h || !row_lib) return GSK_EINVAL;
+  memcpy(row_lib, h->row_lib.data(), (size_t)h->M * sizeof(int32_t));
+  return GSK_OK;
+}
+
+int gsk_spmm(gsk_handle h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
+             void* stream) {
+  if (!h) return GSK_EINVAL;
+  return gsk::spmm_impl(h, which, precision, W, X, Y, n_rep, stream);
+}
+
 int gsk_last_stats(gsk_handle h, gsk_stats* out) {
   if (!h || !out) return GSK_EINVAL;
   *out = h->last;

@@ -14,6 +14,8 @@ constexpr int kThreads = 256;             // threads per CTA of the row kernels
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxW = 128;                // widest lane batch
 constexpr int kMaxShifts = 1024;          // shifts per solve (shared-memory bound of the shift kernel)
+constexpr int kRedGroup = 16;             // CTAs per first-level group of the grid reduction
+constexpr int kMaxRedCtas = 4096;         // CTAs of a reducing kernel
 
 // ---------------------------------------------------------------------------
 // Block layout of A and B (identical pattern), atoms in the library's order.
@@ -81,8 +83,10 @@ struct LaneCtl {
   int* step;           // outer steps executed
   int* unfinished;     // lanes busy + jobs queued
   int* cg_total;       // total CG iterations (all passes), for statistics
-  unsigned int* red_counter;   // arrival counter of the last-CTA reduction
-  double* partials;            // n_ctas * W partial sums
+  unsigned int* red_counter;   // arrival counter of the second reduction level
+  unsigned int* grp_counter;   // arrival counters of the first level (kMaxRedCtas / kRedGroup)
+  double* partials;            // per-CTA partial sums (CTA * W + lane)
+  double* grp_partials;        // per-group partial sums (group * W + lane)
 };
 
 // Read-only description of the job list of one solve.
@@ -202,6 +206,36 @@ struct RedArgs {
 __device__ void finalize_lane(const RedArgs& r, int lane, double s);
 __device__ void finalize_all(const RedArgs& r);
 
+// Fixed-order sum over CTAs [b0, b1) of src[b * W + l] for every lane l, by
+// all threads of the CTA (parts = blockDim / W partial sums per lane, four
+// independent loads in flight per thread), folded into out[l] by thread l.
+__device__ __forceinline__ double fold_rows(const double* __restrict__ src, int b0, int b1, int W,
+                                            double (*sm)[kMaxW]) {
+  const int parts = kThreads / W;
+  const int l = threadIdx.x % W;
+  const int pidx = threadIdx.x / W;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int b = b0 + pidx;
+  for (; b + 3 * parts < b1; b += 4 * parts) {
+    s0 += __ldcg(&src[(size_t)b * W + l]);
+    s1 += __ldcg(&src[(size_t)(b + parts) * W + l]);
+    s2 += __ldcg(&src[(size_t)(b + 2 * parts) * W + l]);
+    s3 += __ldcg(&src[(size_t)(b + 3 * parts) * W + l]);
+  }
+  for (; b < b1; b += parts) s0 += __ldcg(&src[(size_t)b * W + l]);
+  __syncthreads();
+  sm[pidx][l] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < W)
+    for (int p = 0; p < parts; ++p) t += sm[p][threadIdx.x];
+  return t;
+}
+
+// Two-level deterministic reduction across the grid: each CTA writes its
+// per-lane partial; the last CTA to arrive in each group of kRedGroup CTAs
+// folds the group (fixed order); the last group to arrive folds the group
+// sums and runs the finalisation. Counters are reset by their last user.
 template <int L>
 __device__ __forceinline__ void lane_reduce_commit(const double (&mine)[L], const RedArgs& r) {
   __shared__ double sm[kWarps][kMaxW];
@@ -220,28 +254,31 @@ __device__ __forceinline__ void lane_reduce_commit(const double (&mine)[L], cons
   }
   __threadfence();
   __syncthreads();
+  const int grp = blockIdx.x / kRedGroup;
+  const int n_grp = (gridDim.x + kRedGroup - 1) / kRedGroup;
+  const int g0 = grp * kRedGroup;
+  const int g1 = min((int)gridDim.x, g0 + kRedGroup);
   if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(r.c.red_counter, 1u);
-    is_last = (prev == gridDim.x - 1);
+    const unsigned prev = atomicAdd(&r.c.grp_counter[grp], 1u);
+    is_last = (prev == (unsigned)(g1 - g0 - 1));
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int parts = kThreads / W;
-  const int l = threadIdx.x % W;
-  const int pidx = threadIdx.x / W;
-  double s = 0.0;
-  if (pidx < parts) {
-    for (int b = pidx; b < (int)gridDim.x; b += parts) s += __ldcg(&r.c.partials[(size_t)b * W + l]);
+  const double gs = fold_rows(r.c.partials, g0, g1, W, sm);
+  if (threadIdx.x < W) r.c.grp_partials[(size_t)grp * W + threadIdx.x] = gs;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    r.c.grp_counter[grp] = 0u;
+    const unsigned prev = atomicAdd(r.c.red_counter, 1u);
+    is_last = (prev == (unsigned)(n_grp - 1));
   }
   __syncthreads();
-  if (pidx < parts) sm[pidx][l] = s;
-  __syncthreads();
-  if (threadIdx.x < W) {
-    double t = 0.0;
-    for (int p = 0; p < parts; ++p) t += sm[p][threadIdx.x];
-    finalize_lane(r, threadIdx.x, t);
-  }
+  if (!is_last) return;
+  __threadfence();
+  const double t = fold_rows(r.c.grp_partials, 0, n_grp, W, sm);
+  if (threadIdx.x < W) finalize_lane(r, threadIdx.x, t);
   __syncthreads();
   if (threadIdx.x == 0) {
     finalize_all(r);

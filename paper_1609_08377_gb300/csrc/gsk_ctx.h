@@ -80,4 +80,6 @@ namespace gsk {
 int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols,
                const int32_t* cols, const gsk_options* opt, double* G, int32_t* iters,
                int32_t* status, double* resid);
+int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
+              void* stream);
 }

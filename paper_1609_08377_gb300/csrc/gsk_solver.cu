@@ -228,86 +228,140 @@ __device__ __forceinline__ T fmadd(T a, T b, T c) { return fma(a, b, c); }
 template <>
 __device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Product of one atom's block row with W lanes of X; acc[a][i] for row a, lane lane0+i.
+// Block kernels of the SpMM: one neighbour block times L lanes of X.
+// 4-orbital row atom, 4-orbital neighbour: 4 X rows, 4 value columns.
+template <typename TV, typename TX, typename TA, int L>
+__device__ __forceinline__ void blk_4x4(const TV* __restrict__ v, const TX* __restrict__ xp, int W,
+                                        TA (&acc)[4][L]) {
+  TX x0[L], x1[L], x2[L], x3[L];
+  ld_lanes<TX, L>(xp, x0);
+  ld_lanes<TX, L>(xp + W, x1);
+  ld_lanes<TX, L>(xp + 2 * W, x2);
+  ld_lanes<TX, L>(xp + 3 * W, x3);
+  const Quad<TV> c0 = ld_quad(v), c1 = ld_quad(v + 4), c2 = ld_quad(v + 8), c3 = ld_quad(v + 12);
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const TA y0 = TA(x0[i]), y1 = TA(x1[i]), y2 = TA(x2[i]), y3 = TA(x3[i]);
+    acc[0][i] = fmadd<TA>(TA(c0.x), y0, fmadd<TA>(TA(c1.x), y1, fmadd<TA>(TA(c2.x), y2, fmadd<TA>(TA(c3.x), y3, acc[0][i]))));
+    acc[1][i] = fmadd<TA>(TA(c0.y), y0, fmadd<TA>(TA(c1.y), y1, fmadd<TA>(TA(c2.y), y2, fmadd<TA>(TA(c3.y), y3, acc[1][i]))));
+    acc[2][i] = fmadd<TA>(TA(c0.z), y0, fmadd<TA>(TA(c1.z), y1, fmadd<TA>(TA(c2.z), y2, fmadd<TA>(TA(c3.z), y3, acc[2][i]))));
+    acc[3][i] = fmadd<TA>(TA(c0.w), y0, fmadd<TA>(TA(c1.w), y1, fmadd<TA>(TA(c2.w), y2, fmadd<TA>(TA(c3.w), y3, acc[3][i]))));
+  }
+}
+// 4-orbital row atom, 1-orbital neighbour: 1 X row, one value per row.
+template <typename TV, typename TX, typename TA, int L>
+__device__ __forceinline__ void blk_4x1(const TV* __restrict__ v, const TX* __restrict__ xp, TA (&acc)[4][L]) {
+  TX x0[L];
+  ld_lanes<TX, L>(xp, x0);
+  const Quad<TV> c0 = ld_quad(v);
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const TA y0 = TA(x0[i]);
+    acc[0][i] = fmadd<TA>(TA(c0.x), y0, acc[0][i]);
+    acc[1][i] = fmadd<TA>(TA(c0.y), y0, acc[1][i]);
+    acc[2][i] = fmadd<TA>(TA(c0.z), y0, acc[2][i]);
+    acc[3][i] = fmadd<TA>(TA(c0.w), y0, acc[3][i]);
+  }
+}
+// 1-orbital row atom: four X rows (one 4-orbital neighbour, or four 1-orbital
+// neighbours) against four values.
+template <typename TV, typename TX, typename TA, int L>
+__device__ __forceinline__ void blk_1x4(const TV* __restrict__ v, const TX* __restrict__ xa,
+                                        const TX* __restrict__ xb, const TX* __restrict__ xc,
+                                        const TX* __restrict__ xd, TA (&acc)[4][L]) {
+  TX x0[L], x1[L], x2[L], x3[L];
+  ld_lanes<TX, L>(xa, x0);
+  ld_lanes<TX, L>(xb, x1);
+  ld_lanes<TX, L>(xc, x2);
+  ld_lanes<TX, L>(xd, x3);
+  const Quad<TV> c0 = ld_quad(v);
+#pragma unroll
+  for (int i = 0; i < L; ++i)
+    acc[0][i] = fmadd<TA>(TA(c0.x), TA(x0[i]), fmadd<TA>(TA(c0.y), TA(x1[i]),
+                fmadd<TA>(TA(c0.z), TA(x2[i]), fmadd<TA>(TA(c0.w), TA(x3[i]), acc[0][i]))));
+}
+
+// Product of one atom's block row with W lanes of X; acc[a][i] for row a,
+// lane lane0+i. Neighbour rows are fetched 32 at a time with one coalesced
+// load per warp and broadcast by shuffles; two neighbour blocks are processed
+// per iteration so that their loads are in flight together.
 template <typename TV, typename TX, typename TA, int L>
 __device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __restrict__ val,
                                                  const TX* __restrict__ X, int W, int lane0, int I,
                                                  TA (&acc)[4][L], int& oI, int& r0) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   oI = g.atom_orb[I];
   r0 = g.atom_roff[I];
   const TV* v = val + g.val_ptr[I];
-  int e = g.nbr_ptr[I];
+  const int e0 = g.nbr_ptr[I];
   const int em = g.nbr_mid[I];
   const int e1 = g.nbr_ptr[I + 1];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int i = 0; i < L; ++i) acc[a][i] = TA(0);
+  auto xrow = [&](int r) { return X + (size_t)r * W + lane0; };
   if (oI == 4) {
-    for (; e < em; ++e) {
-      const TX* xp = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
-      TX x0[L], x1[L], x2[L], x3[L];
-      ld_lanes<TX, L>(xp, x0);
-      ld_lanes<TX, L>(xp + W, x1);
-      ld_lanes<TX, L>(xp + 2 * W, x2);
-      ld_lanes<TX, L>(xp + 3 * W, x3);
-      const Quad<TV> c0 = ld_quad(v), c1 = ld_quad(v + 4), c2 = ld_quad(v + 8), c3 = ld_quad(v + 12);
-      v += 16;
-#pragma unroll
-      for (int i = 0; i < L; ++i) {
-        const TA y0 = TA(x0[i]), y1 = TA(x1[i]), y2 = TA(x2[i]), y3 = TA(x3[i]);
-        acc[0][i] = fmadd<TA>(TA(c0.x), y0, fmadd<TA>(TA(c1.x), y1, fmadd<TA>(TA(c2.x), y2, fmadd<TA>(TA(c3.x), y3, acc[0][i]))));
-        acc[1][i] = fmadd<TA>(TA(c0.y), y0, fmadd<TA>(TA(c1.y), y1, fmadd<TA>(TA(c2.y), y2, fmadd<TA>(TA(c3.y), y3, acc[1][i]))));
-        acc[2][i] = fmadd<TA>(TA(c0.z), y0, fmadd<TA>(TA(c1.z), y1, fmadd<TA>(TA(c2.z), y2, fmadd<TA>(TA(c3.z), y3, acc[2][i]))));
-        acc[3][i] = fmadd<TA>(TA(c0.w), y0, fmadd<TA>(TA(c1.w), y1, fmadd<TA>(TA(c2.w), y2, fmadd<TA>(TA(c3.w), y3, acc[3][i]))));
+    for (int base = e0; base < em; base += 32) {
+      const int cnt = min(32, em - base);
+      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int t = 0;
+      for (; t + 2 <= cnt; t += 2) {
+        const int ra = __shfl_sync(kFull, myr, t);
+        const int rb = __shfl_sync(kFull, myr, t + 1);
+        blk_4x4<TV, TX, TA, L>(v, xrow(ra), W, acc);
+        blk_4x4<TV, TX, TA, L>(v + 16, xrow(rb), W, acc);
+        v += 32;
+      }
+      if (t < cnt) {
+        blk_4x4<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), W, acc);
+        v += 16;
       }
     }
-    for (; e < e1; ++e) {
-      const TX* xp = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
-      TX x0[L];
-      ld_lanes<TX, L>(xp, x0);
-      const Quad<TV> c0 = ld_quad(v);
-      v += 4;
-#pragma unroll
-      for (int i = 0; i < L; ++i) {
-        const TA y0 = TA(x0[i]);
-        acc[0][i] = fmadd<TA>(TA(c0.x), y0, acc[0][i]);
-        acc[1][i] = fmadd<TA>(TA(c0.y), y0, acc[1][i]);
-        acc[2][i] = fmadd<TA>(TA(c0.z), y0, acc[2][i]);
-        acc[3][i] = fmadd<TA>(TA(c0.w), y0, acc[3][i]);
+    for (int base = em; base < e1; base += 32) {
+      const int cnt = min(32, e1 - base);
+      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int t = 0;
+      for (; t + 4 <= cnt; t += 4) {
+        blk_4x1<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), acc);
+        blk_4x1<TV, TX, TA, L>(v + 4, xrow(__shfl_sync(kFull, myr, t + 1)), acc);
+        blk_4x1<TV, TX, TA, L>(v + 8, xrow(__shfl_sync(kFull, myr, t + 2)), acc);
+        blk_4x1<TV, TX, TA, L>(v + 12, xrow(__shfl_sync(kFull, myr, t + 3)), acc);
+        v += 16;
+      }
+      for (; t < cnt; ++t) {
+        blk_4x1<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), acc);
+        v += 4;
       }
     }
   } else {
-    for (; e < em; ++e) {
-      const TX* xp = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
-      TX x0[L], x1[L], x2[L], x3[L];
-      ld_lanes<TX, L>(xp, x0);
-      ld_lanes<TX, L>(xp + W, x1);
-      ld_lanes<TX, L>(xp + 2 * W, x2);
-      ld_lanes<TX, L>(xp + 3 * W, x3);
-      const Quad<TV> c0 = ld_quad(v);
-      v += 4;
-#pragma unroll
-      for (int i = 0; i < L; ++i)
-        acc[0][i] = fmadd<TA>(TA(c0.x), TA(x0[i]), fmadd<TA>(TA(c0.y), TA(x1[i]),
-                    fmadd<TA>(TA(c0.z), TA(x2[i]), fmadd<TA>(TA(c0.w), TA(x3[i]), acc[0][i]))));
+    for (int base = e0; base < em; base += 32) {
+      const int cnt = min(32, em - base);
+      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int t = 0;
+      for (; t + 2 <= cnt; t += 2) {
+        const TX* xa = xrow(__shfl_sync(kFull, myr, t));
+        const TX* xb = xrow(__shfl_sync(kFull, myr, t + 1));
+        blk_1x4<TV, TX, TA, L>(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
+        blk_1x4<TV, TX, TA, L>(v + 4, xb, xb + W, xb + 2 * W, xb + 3 * W, acc);
+        v += 8;
+      }
+      if (t < cnt) {
+        const TX* xa = xrow(__shfl_sync(kFull, myr, t));
+        blk_1x4<TV, TX, TA, L>(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
+        v += 4;
+      }
     }
-    for (; e < e1; e += 4) {
-      const TX* xa = X + (size_t)__ldg(&g.nbr_roff[e]) * W + lane0;
-      const TX* xb = X + (size_t)__ldg(&g.nbr_roff[e + 1]) * W + lane0;
-      const TX* xc = X + (size_t)__ldg(&g.nbr_roff[e + 2]) * W + lane0;
-      const TX* xd = X + (size_t)__ldg(&g.nbr_roff[e + 3]) * W + lane0;
-      TX x0[L], x1[L], x2[L], x3[L];
-      ld_lanes<TX, L>(xa, x0);
-      ld_lanes<TX, L>(xb, x1);
-      ld_lanes<TX, L>(xc, x2);
-      ld_lanes<TX, L>(xd, x3);
-      const Quad<TV> c0 = ld_quad(v);
-      v += 4;
-#pragma unroll
-      for (int i = 0; i < L; ++i)
-        acc[0][i] = fmadd<TA>(TA(c0.x), TA(x0[i]), fmadd<TA>(TA(c0.y), TA(x1[i]),
-                    fmadd<TA>(TA(c0.z), TA(x2[i]), fmadd<TA>(TA(c0.w), TA(x3[i]), acc[0][i]))));
+    // 1-orbital neighbours come padded to a multiple of 4
+    for (int base = em; base < e1; base += 32) {
+      const int cnt = min(32, e1 - base);
+      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      for (int t = 0; t < cnt; t += 4) {
+        blk_1x4<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), xrow(__shfl_sync(kFull, myr, t + 1)),
+                               xrow(__shfl_sync(kFull, myr, t + 2)), xrow(__shfl_sync(kFull, myr, t + 3)), acc);
+        v += 4;
+      }
     }
   }
 }
@@ -1152,7 +1206,10 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
 
   // lane control block
   const int n_red = std::max(P.grid_rows, P.grid_vec);
-  const size_t lane_bytes = 64 * kMaxW * sizeof(double) + (size_t)n_red * kMaxW * sizeof(double) + 256;
+  if (n_red > kMaxRedCtas) return GSK_ENOTSUP;
+  const int n_grp_max = (kMaxRedCtas + kRedGroup - 1) / kRedGroup;
+  const size_t lane_bytes = 64 * kMaxW * sizeof(double) + (size_t)n_red * kMaxW * sizeof(double) +
+                            (size_t)n_grp_max * kMaxW * sizeof(double) + n_grp_max * sizeof(unsigned) + 256;
   if (h->ws_lane.ensure(lane_bytes) != cudaSuccess) return GSK_ENOMEM;
   char* lb = h->ws_lane.as<char>();
   LaneCtl c{};
@@ -1169,6 +1226,10 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
     c.cg_total = scal + 4;
     c.red_counter = reinterpret_cast<unsigned int*>(scal + 5);
     c.partials = reinterpret_cast<double*>(lb + o);
+    o += (size_t)n_red * kMaxW * sizeof(double);
+    c.grp_partials = reinterpret_cast<double*>(lb + o);
+    o += (size_t)n_grp_max * kMaxW * sizeof(double);
+    c.grp_counter = reinterpret_cast<unsigned int*>(lb + o);
   }
 
   // job arrays
@@ -1326,6 +1387,60 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   if (iters) memcpy(iters, h_it.data(), n_cols * sizeof(int32_t));
   if (status) memcpy(status, h_st.data(), n_cols * sizeof(int32_t));
   if (resid) memcpy(resid, h_rs.data(), n_cols * sizeof(double));
+  return GSK_OK;
+}
+
+}  // namespace gsk
+
+// ===========================================================================
+// Standalone block SpMM (same kernel and launch shape as inside the solve)
+// ===========================================================================
+namespace gsk {
+
+int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
+              void* stream) {
+  if ((which != 0 && which != 1) || (precision != GSK_FP64 && precision != GSK_MIXED) || n_rep < 0 || !X || !Y)
+    return GSK_EINVAL;
+  if (W != 32 && W != 64 && W != 128) return GSK_EINVAL;
+  if (precision == GSK_FP64 && W == 128) return GSK_ENOTSUP;
+  if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = h->lay.n_ctas;
+  const int n_grp_max = (kMaxRedCtas + kRedGroup - 1) / kRedGroup;
+  const size_t lane_bytes = 64 * kMaxW * sizeof(double) + (size_t)grid * kMaxW * sizeof(double) +
+                            (size_t)n_grp_max * kMaxW * sizeof(double) + n_grp_max * sizeof(unsigned) + 256;
+  if (grid > kMaxRedCtas) return GSK_ENOTSUP;
+  if (h->ws_lane.ensure(lane_bytes) != cudaSuccess) return GSK_ENOMEM;
+  char* lb = h->ws_lane.as<char>();
+  if (cudaMemsetAsync(lb, 0, lane_bytes, s) != cudaSuccess) return GSK_ECUDA;
+  LaneCtl c{};
+  c.red_out = reinterpret_cast<double*>(lb);
+  c.red_counter = reinterpret_cast<unsigned int*>(lb + kMaxW * sizeof(double));
+  c.partials = reinterpret_cast<double*>(lb + 2 * kMaxW * sizeof(double));
+  c.grp_partials = c.partials + (size_t)grid * kMaxW;
+  c.grp_counter = reinterpret_cast<unsigned int*>(c.grp_partials + (size_t)n_grp_max * kMaxW);
+  RedArgs r{};
+  r.c = c;
+  r.fin = FIN_SUM;
+  r.W = W;
+  const dim3 blk(kThreads), grd(grid);
+  for (int i = 0; i < n_rep; ++i) {
+    if (precision == GSK_FP64) {
+      SpmmArgs<double, double, double> a{h->lay, (which ? h->d_B64 : h->d_A64).as<double>(),
+                                         static_cast<const double*>(X), static_cast<double*>(Y),
+                                         nullptr, nullptr, nullptr, r};
+      if (W == 32) k_spmm<double, double, double, double, 1, SP_DOT><<<grd, blk, 0, s>>>(a);
+      else k_spmm<double, double, double, double, 2, SP_DOT><<<grd, blk, 0, s>>>(a);
+    } else {
+      SpmmArgs<float, float, float> a{h->lay, (which ? h->d_B32 : h->d_A32).as<float>(),
+                                      static_cast<const float*>(X), static_cast<float*>(Y),
+                                      nullptr, nullptr, nullptr, r};
+      if (W == 32) k_spmm<float, float, float, float, 1, SP_DOT><<<grd, blk, 0, s>>>(a);
+      else if (W == 64) k_spmm<float, float, float, float, 2, SP_DOT><<<grd, blk, 0, s>>>(a);
+      else k_spmm<float, float, float, float, 4, SP_DOT><<<grd, blk, 0, s>>>(a);
+    }
+    if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
+  }
   return GSK_OK;
 }
 

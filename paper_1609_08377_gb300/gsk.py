@@ -64,6 +64,8 @@ def _load() -> C.CDLL:
         "gsk_trace": (C.c_int, [P, I32, P, P, I32, P]),
         "gsk_strerror": (C.c_char_p, [C.c_int]),
         "gsk_last_stats": (C.c_int, [P, P]),
+        "gsk_row_order": (C.c_int, [P, P]),
+        "gsk_spmm": (C.c_int, [P, I32, I32, I32, P, P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -162,6 +164,16 @@ class Solver:
         st = Stats()
         _check(_lib.gsk_last_stats(self._h, C.byref(st)), "gsk_last_stats")
         return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def row_order(self) -> np.ndarray:
+        out = np.empty(self.M, dtype=np.int32)
+        _check(_lib.gsk_row_order(self._h, _ptr(out)), "gsk_row_order")
+        return out
+
+    def spmm(self, which: int, precision: int, W: int, X, Y, n_rep: int = 1, stream=None) -> None:
+        s = getattr(stream, "cuda_stream", stream)
+        _check(_lib.gsk_spmm(self._h, int(which), int(precision), int(W), _ptr(X), _ptr(Y), int(n_rep), s),
+               "gsk_spmm")
 
     def pattern_offsets(self, cols) -> np.ndarray:
         cols = np.ascontiguousarray(cols, dtype=np.int32)
