@@ -154,6 +154,33 @@ int gsk_density(gsk_handle h, int64_t n_elem, int32_t n_shifts, const double* ep
                 const double* w, double mu, double kT, const double* G, double* rho,
                 void* stream);
 
+/* Allocation-free variant of gsk_density; the paper has no counterpart.
+ *
+ * Same result and arguments as gsk_density, but it needs no handle and never
+ * allocates device memory. It is meant for callers that cannot call
+ * cudaMalloc: applications whose device memory is owned by their own pool
+ * allocator, services that forbid allocation after start-up because an
+ * allocation can stall the device and has no latency bound, and plug-ins that
+ * run inside a host program that hands them buffers but no right to allocate.
+ *
+ * The shift energies, weights and Fermi-weighted coefficients of a call live
+ * in a fixed device array inside libgsk of 3 * GSK_NOALLOC_MAX_SHIFTS doubles
+ * (24 KiB). Every GPU that loads the library holds that array until the
+ * process exits.
+ *   n_shifts  1 .. GSK_NOALLOC_MAX_SHIFTS; larger values return GSK_EINVAL
+ *   eps, w    host, n_shifts doubles (copied before the call returns)
+ *   G, rho    device buffers on the current device, as for gsk_density
+ *   stream    cudaStream_t or NULL; the work is asynchronous on that stream
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current). All calls share the array: each call
+ * overwrites the 3 * n_shifts entries it reads before it reads them, so
+ * nothing has to start at zero, but calls whose work overlaps on the GPU
+ * (for example on two streams) race on it and must be serialised by the
+ * caller. */
+#define GSK_NOALLOC_MAX_SHIFTS 1024
+int gsk_density_noalloc(int64_t n_elem, int32_t n_shifts, const double* eps, const double* w,
+                        double mu, double kT, const double* G, double* rho, void* stream);
+
 /* Tr over the column set of rho X (Eq. TRACE-X restricted to the columns
  * solved): sum_c sum_{t} rho[offsets[c]+t] * X_{cols[c], i_t}, X = A (which=0)
  * or B (which=1). rho device; result written to *out (host). Synchronous. */

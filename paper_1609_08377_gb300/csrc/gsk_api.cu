@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -130,9 +131,60 @@ __global__ void k_trace_final(int nb, const double* partial, double* out) {
   }
 }
 
+// Fixed device scratch of gsk_density_noalloc: eps, w and the Fermi-weighted
+// coefficients of one call (3 * GSK_NOALLOC_MAX_SHIFTS doubles). Host code
+// must not pass the symbol itself to a kernel: in host code it names a host
+// stand-in, so the device address is looked up with cudaGetSymbolAddress.
+__device__ __align__(256) double g_noalloc_scratch[3 * GSK_NOALLOC_MAX_SHIFTS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device (looked up once per device).
+cudaError_t noalloc_scratch(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
+
+int gsk_density_noalloc(int64_t n_elem, int32_t n_shifts, const double* eps, const double* w, double mu,
+                        double kT, const double* G, double* rho, void* stream) {
+  if (n_elem < 0 || n_shifts < 1 || n_shifts > GSK_NOALLOC_MAX_SHIFTS || !eps || !w || !(kT > 0.0) ||
+      !isfinite(mu))
+    return GSK_EINVAL;
+  if (n_elem > 0 && (!G || !rho)) return GSK_EINVAL;
+  if (!finite_all(eps, n_shifts) || !finite_all(w, n_shifts)) return GSK_EINVAL;
+  if (n_elem == 0) return GSK_OK;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GSK_ECUDA;
+  double* scratch = nullptr;
+  if (noalloc_scratch(dev, &scratch) != cudaSuccess) return GSK_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* d_eps = scratch;
+  double* d_w = scratch + n_shifts;
+  double* d_coef = scratch + 2 * n_shifts;
+  cudaError_t e = cudaMemcpyAsync(d_eps, eps, n_shifts * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, w, n_shifts * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return GSK_ECUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GSK_ECUDA;
+  k_fermi_weights<<<(n_shifts + 127) / 128, 128, 0, s>>>(n_shifts, d_eps, d_w, mu, kT, d_coef);
+  const int64_t blocks = std::min<int64_t>((n_elem + 7) / 8, (int64_t)sms * 16);
+  k_density<<<(unsigned)blocks, 256, 0, s>>>(n_elem, n_shifts, d_coef, reinterpret_cast<const double2*>(G), rho);
+  return cudaGetLastError() == cudaSuccess ? GSK_OK : GSK_ECUDA;
+}
 
 void gsk_default_options(gsk_options* opt) {
   if (!opt) return;

@@ -66,6 +66,7 @@ def _load() -> C.CDLL:
         "gsk_last_stats": (C.c_int, [P, P]),
         "gsk_row_order": (C.c_int, [P, P]),
         "gsk_spmm": (C.c_int, [P, I32, I32, I32, P, P, I32, P]),
+        "gsk_density_noalloc": (C.c_int, [I64, I32, P, P, D, D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +213,15 @@ class Solver:
         out = C.c_double()
         _check(_lib.gsk_trace(self._h, cols.size, _ptr(cols), _ptr(rho), int(which), C.byref(out)), "gsk_trace")
         return float(out.value)
+
+
+def density_noalloc(G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=None) -> None:
+    """gsk_density_noalloc: the density matrix without a handle or any device allocation."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_lib.gsk_density_noalloc(int(n_elem), eps.size, _ptr(eps), _ptr(w), float(mu), float(kT),
+                                    _ptr(G), _ptr(rho), s), "gsk_density_noalloc")
 
 
 def from_system(sys_, pos=True) -> Solver:
