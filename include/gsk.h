@@ -28,6 +28,7 @@
 #ifndef GSK_H
 #define GSK_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -52,6 +53,9 @@ extern "C" {
 /* ----- option values ------------------------------------------------------ */
 #define GSK_FP64 0           /* every product and vector update in FP64 */
 #define GSK_MIXED 1          /* FP32 inner B-solve, FP64 residual refinement, FP64 Lanczos */
+#define GSK_MIXED_DF 2       /* as GSK_MIXED, with the FP64-accuracy parts (A-products, refinement
+                                residuals, Lanczos vectors, inner products) in double-float
+                                arithmetic: pairs of FP32 numbers, 48-bit significand */
 
 #define GSK_SCHED_FIFO 0     /* columns enter the work queue in the given order */
 #define GSK_SCHED_LEARNED 1  /* longest predicted iteration count first (needs a model) */
@@ -84,12 +88,12 @@ typedef struct {
 /* Solver options. Zero-initialise and set what you need; gsk_default_options
  * fills the defaults listed here. */
 typedef struct {
-  int32_t precision;    /* GSK_FP64 (default) or GSK_MIXED */
+  int32_t precision;    /* GSK_FP64 (default), GSK_MIXED or GSK_MIXED_DF */
   double tol;           /* relative residual ||e_j - (z B - A) x||_2 for every shift; default 1e-8 */
   int32_t max_iter;     /* Lanczos steps per column; default 20000 */
   int32_t batch_w;      /* lanes (columns in flight): 32, 64 or 128; 0 = autotune (default) */
   int32_t refine;       /* GSK_MIXED only: 1 = FP64 residual correction of each B-solve (default), 0 = none */
-  int32_t sched;        /* GSK_SCHED_FIFO (default) or GSK_SCHED_LEARNED */
+  int32_t sched;        /* GSK_SCHED_FIFO (default) or GSK_SCHED_LEARNED (model set with gsk_set_sched_model) */
   double inner_tol;     /* relative residual of each B-solve; 0 = default (1e-12 FP64, 1e-6 per FP32 pass) */
   int32_t max_inner;    /* CG iteration cap per B-solve pass; default 200 */
   int32_t use_graph;    /* 1 = run the solve as one captured CUDA graph with device-side loops (default) */
@@ -101,7 +105,7 @@ void gsk_default_options(gsk_options* opt);
 
 /* Build a solver handle from A, B (same pattern, symmetric) and the orbital
  * map. Copies the matrices to the device in the library's block layout
- * (FP64, plus an FP32 copy for GSK_MIXED). Returns GSK_EINVAL for malformed
+ * (FP64, plus FP32 and FP32-pair copies for the mixed modes). Returns GSK_EINVAL for malformed
  * input or non-finite values, GSK_ENOTSPD when some B_ii <= 0 or a row of B is
  * not strictly diagonally dominant (a sufficient test for positive
  * definiteness; the library requires it). The handle owns every device
@@ -201,6 +205,50 @@ int gsk_row_order(gsk_handle h, int32_t* row_lib);
  *   stream    cudaStream_t or NULL. Asynchronous on that stream. */
 int gsk_spmm(gsk_handle h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y,
              int32_t n_rep, void* stream);
+
+/* ----- learned column scheduler ---------------------------------------------
+ * A 16 -> 64 -> 64 -> 1 multilayer perceptron (tanh, FP32) predicts log(number
+ * of Lanczos steps) of a column from 16 per-column features; with
+ * sched = GSK_SCHED_LEARNED, gsk_solve hands out columns longest predicted
+ * first, which shortens the tail of the work queue (the load imbalance from
+ * structural disorder of Sec. IV-C). Every column still iterates to tol.
+ * Parameters: one flat FP32 vector W1 [64][16], b1 [64], W2 [64][64], b2 [64],
+ * w3 [64], b3 [1]. Normalisation: 32 floats, mean[16] then std[16] (> 0);
+ * the network sees (feature - mean) / std. Features of column j = (atom J,
+ * orbital a) with damping eta: log(eta), 0.1/eta, entries of row j / 100,
+ * neighbour atoms of J / 50, 4-orbital neighbours / 20, 1-orbital neighbours
+ * / 40, [J has 4 orbitals], a/3, A_jj/10, sum_{i!=j}|A_ij|/10,
+ * sum_{i!=j}|B_ij|, sqrt(sum_{i!=j} A_ij^2)/10, A_jj^2/100, B_jj,
+ * log(1 + sum_i |A_ij|), 1. */
+#define GSK_MLP_IN 16
+#define GSK_MLP_HIDDEN 64
+#define GSK_MLP_NPARAM 5313
+
+/* Features of columns cols[0..n) with dampings eta (host arrays) into feat
+ * (device, n x 16 row-major). Synchronous. */
+int gsk_features(gsk_handle h, int32_t n_cols, const int32_t* cols, const double* eta, float* feat,
+                 void* stream);
+
+/* y[s] = MLP(params, (feat[s] - mean) / std) for n samples (all device
+ * pointers, current device). Asynchronous on stream. */
+int gsk_mlp_forward(int32_t n, const float* feat, const float* norm, const float* params, float* y,
+                    void* stream);
+
+/* Bytes of the device workspace gsk_mlp_train_step needs for n samples. */
+size_t gsk_mlp_workspace_bytes(int32_t n);
+
+/* One full-batch step on the mean squared error (1/n) sum (y - target)^2:
+ * gradient by backpropagation (deterministic fixed-order sums), then, if
+ * t >= 1, one Adam update (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias
+ * correction with step number t). grad (n_param floats) and loss (1 float,
+ * the loss before the update) are optional outputs. All pointers device;
+ * work holds gsk_mlp_workspace_bytes(n) bytes. Asynchronous on stream. */
+int gsk_mlp_train_step(int32_t n, const float* feat, const float* norm, const float* target, float* params,
+                       float* adam_m, float* adam_v, int32_t t, float lr, float* grad, float* loss,
+                       void* work, void* stream);
+
+/* Install a trained model (host arrays) on the handle for GSK_SCHED_LEARNED. */
+int gsk_set_sched_model(gsk_handle h, const float* params, const float* norm);
 
 /* Counters of the last gsk_solve on this handle. */
 typedef struct {

@@ -401,12 +401,21 @@ int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_ha
   }
   // FP32 copies for the mixed-precision inner solve
   std::vector<float> va32(nval), vb32(nval);
+  std::vector<float> va2(2 * nval), vb2(2 * nval);     // double-float pairs (hi, lo)
   for (int64_t t = 0; t < nval; ++t) {
     va32[t] = (float)va[t];
     vb32[t] = (float)vbv[t];
+    va2[2 * t] = va32[t];
+    va2[2 * t + 1] = (float)(va[t] - (double)va32[t]);
+    vb2[2 * t] = vb32[t];
+    vb2[2 * t + 1] = (float)(vbv[t] - (double)vb32[t]);
   }
 
+  std::vector<float> rowfeat;
+  gsk::build_row_features(A, B, map, rowfeat);
+
   cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = upload(h->d_rowfeat, rowfeat);
   if (e == cudaSuccess) e = upload(h->d_atom_roff, roff);
   if (e == cudaSuccess) e = upload(h->d_atom_orb, orb);
   if (e == cudaSuccess) e = upload(h->d_nbr_ptr, nbr_ptr);
@@ -417,6 +426,8 @@ int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_ha
   if (e == cudaSuccess) e = upload(h->d_B64, vbv);
   if (e == cudaSuccess) e = upload(h->d_A32, va32);
   if (e == cudaSuccess) e = upload(h->d_B32, vb32);
+  if (e == cudaSuccess) e = upload(h->d_A2, va2);
+  if (e == cudaSuccess) e = upload(h->d_B2, vb2);
   if (e == cudaErrorMemoryAllocation) return fail(GSK_ENOMEM);
   if (e != cudaSuccess) return fail(GSK_ECUDA);
 

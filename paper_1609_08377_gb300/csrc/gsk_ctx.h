@@ -56,9 +56,16 @@ struct gsk_ctx {
   // device block layout
   gsk::Layout lay{};
   gsk::DevBuf d_atom_roff, d_atom_orb, d_nbr_ptr, d_nbr_mid, d_nbr_roff, d_val_ptr;
-  gsk::DevBuf d_A64, d_B64, d_A32, d_B32;
+  gsk::DevBuf d_A64, d_B64, d_A32, d_B32, d_A2, d_B2;   // FP64, FP32, FP32 pairs (hi, lo)
 
   gsk_stats last{};
+
+  // learned scheduler
+  gsk::DevBuf d_rowfeat;          // M x 14 static per-row features
+  gsk::DevBuf d_sched_params;     // GSK_MLP_NPARAM floats
+  gsk::DevBuf d_sched_norm;       // 2 * GSK_MLP_IN floats
+  gsk::DevBuf ws_sched;           // feature / prediction scratch
+  bool sched_ready = false;
 
   // solver workspace (grown on demand)
   gsk::DevBuf ws_vec;      // Lanczos / CG vectors
@@ -70,13 +77,17 @@ struct gsk_ctx {
 
   ~gsk_ctx() {
     gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr,
-                          &d_A64, &d_B64, &d_A32, &d_B32, &ws_vec, &ws_lane, &ws_jobs,
-                          &ws_shift, &ws_gstage, &ws_misc};
+                          &d_A64, &d_B64, &d_A32, &d_B32, &d_A2, &d_B2, &ws_vec, &ws_lane, &ws_jobs,
+                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched};
     for (auto* b : all) b->release();
   }
 };
 
 namespace gsk {
+inline size_t align_up_sz(size_t x, size_t a) { return (x + a - 1) / a * a; }
+void build_row_features(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, std::vector<float>& out);
+int learned_order(gsk_ctx* h, int32_t n_cols, const int32_t* cols, const double* eta_cols, cudaStream_t s,
+                  std::vector<int32_t>& queue);
 int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols,
                const int32_t* cols, const gsk_options* opt, double* G, int32_t* iters,
                int32_t* status, double* resid);

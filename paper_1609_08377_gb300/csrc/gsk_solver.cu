@@ -28,10 +28,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "gsk_common.cuh"
 #include "gsk_ctx.h"
+#include "gsk_df64.cuh"
 
 namespace gsk {
 
@@ -281,14 +283,120 @@ __device__ __forceinline__ void blk_1x4(const TV* __restrict__ v, const TX* __re
                 fmadd<TA>(TA(c0.z), TA(x2[i]), fmadd<TA>(TA(c0.w), TA(x3[i]), acc[0][i]))));
 }
 
+// Block arithmetic policies of the SpMM traversal.
+template <typename TV, typename TX, typename TA, int L>
+struct PlainOps {
+  using V = TV;
+  using X = TX;
+  using Acc = TA;
+  static __device__ __forceinline__ void zero(Acc (&acc)[4][L]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < L; ++i) acc[a][i] = TA(0);
+  }
+  static __device__ __forceinline__ void b44(const V* v, const X* xp, int W, Acc (&acc)[4][L]) {
+    blk_4x4<TV, TX, TA, L>(v, xp, W, acc);
+  }
+  static __device__ __forceinline__ void b41(const V* v, const X* xp, Acc (&acc)[4][L]) {
+    blk_4x1<TV, TX, TA, L>(v, xp, acc);
+  }
+  static __device__ __forceinline__ void b14(const V* v, const X* xa, const X* xb, const X* xc, const X* xd,
+                                             Acc (&acc)[4][L]) {
+    blk_1x4<TV, TX, TA, L>(v, xa, xb, xc, xd, acc);
+  }
+};
+
+// Double-float policy: values are (hi, lo) FP32 pairs, X is double-float
+// (float2) or single (float); every product enters an error-free accumulator.
+__device__ __forceinline__ void ld_quad_df(const float2* __restrict__ p, float2 (&c)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  c[0] = make_float2(a.x, a.y);
+  c[1] = make_float2(a.z, a.w);
+  c[2] = make_float2(b.x, b.y);
+  c[3] = make_float2(b.z, b.w);
+}
+template <typename TX, int L>
+__device__ __forceinline__ void ld_x(const TX* __restrict__ p, TX (&o)[L]) {
+  if constexpr (sizeof(TX) == 8) {   // float2 lanes
+    const float* f = reinterpret_cast<const float*>(p);
+    if constexpr (L == 1) {
+      const float2 v = *reinterpret_cast<const float2*>(f);
+      o[0] = v;
+    } else {
+#pragma unroll
+      for (int h = 0; h < L / 2; ++h) {
+        const float4 v = reinterpret_cast<const float4*>(f)[h];
+        o[2 * h] = make_float2(v.x, v.y);
+        o[2 * h + 1] = make_float2(v.z, v.w);
+      }
+    }
+  } else {
+    ld_lanes<float, L>(reinterpret_cast<const float*>(p), reinterpret_cast<float(&)[L]>(o));
+  }
+}
+template <typename TX, int L>
+struct DfOps {
+  using V = float2;
+  using X = TX;
+  using Acc = dfacc;
+  static __device__ __forceinline__ void zero(Acc (&acc)[4][L]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < L; ++i) acc_zero(acc[a][i]);
+  }
+  static __device__ __forceinline__ void b44(const V* v, const X* xp, int W, Acc (&acc)[4][L]) {
+    X x[4][L];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) ld_x<X, L>(xp + b * W, x[b]);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float2 c[4];
+      ld_quad_df(v + 4 * b, c);
+#pragma unroll
+      for (int i = 0; i < L; ++i)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc_fma(acc[a][i], c[a], x[b][i]);
+    }
+  }
+  static __device__ __forceinline__ void b41(const V* v, const X* xp, Acc (&acc)[4][L]) {
+    X x[L];
+    ld_x<X, L>(xp, x);
+    float2 c[4];
+    ld_quad_df(v, c);
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc_fma(acc[a][i], c[a], x[i]);
+  }
+  static __device__ __forceinline__ void b14(const V* v, const X* xa, const X* xb, const X* xc, const X* xd,
+                                             Acc (&acc)[4][L]) {
+    X x[4][L];
+    ld_x<X, L>(xa, x[0]);
+    ld_x<X, L>(xb, x[1]);
+    ld_x<X, L>(xc, x[2]);
+    ld_x<X, L>(xd, x[3]);
+    float2 c[4];
+    ld_quad_df(v, c);
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc_fma(acc[0][i], c[b], x[b][i]);
+  }
+};
+
 // Product of one atom's block row with W lanes of X; acc[a][i] for row a,
 // lane lane0+i. Neighbour rows are fetched 32 at a time with one coalesced
 // load per warp and broadcast by shuffles; two neighbour blocks are processed
 // per iteration so that their loads are in flight together.
-template <typename TV, typename TX, typename TA, int L>
-__device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __restrict__ val,
-                                                 const TX* __restrict__ X, int W, int lane0, int I,
-                                                 TA (&acc)[4][L], int& oI, int& r0) {
+template <class Ops, int L>
+__device__ __forceinline__ void atom_row_product(const Layout& g, const typename Ops::V* __restrict__ val,
+                                                 const typename Ops::X* __restrict__ X, int W, int lane0, int I,
+                                                 typename Ops::Acc (&acc)[4][L], int& oI, int& r0) {
+  using TV = typename Ops::V;
+  using TX = typename Ops::X;
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   oI = g.atom_orb[I];
@@ -297,10 +405,7 @@ __device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __re
   const int e0 = g.nbr_ptr[I];
   const int em = g.nbr_mid[I];
   const int e1 = g.nbr_ptr[I + 1];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int i = 0; i < L; ++i) acc[a][i] = TA(0);
+  Ops::zero(acc);
   auto xrow = [&](int r) { return X + (size_t)r * W + lane0; };
   if (oI == 4) {
     for (int base = e0; base < em; base += 32) {
@@ -310,12 +415,12 @@ __device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __re
       for (; t + 2 <= cnt; t += 2) {
         const int ra = __shfl_sync(kFull, myr, t);
         const int rb = __shfl_sync(kFull, myr, t + 1);
-        blk_4x4<TV, TX, TA, L>(v, xrow(ra), W, acc);
-        blk_4x4<TV, TX, TA, L>(v + 16, xrow(rb), W, acc);
+        Ops::b44(v, xrow(ra), W, acc);
+        Ops::b44(v + 16, xrow(rb), W, acc);
         v += 32;
       }
       if (t < cnt) {
-        blk_4x4<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), W, acc);
+        Ops::b44(v, xrow(__shfl_sync(kFull, myr, t)), W, acc);
         v += 16;
       }
     }
@@ -324,14 +429,14 @@ __device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __re
       const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
       int t = 0;
       for (; t + 4 <= cnt; t += 4) {
-        blk_4x1<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), acc);
-        blk_4x1<TV, TX, TA, L>(v + 4, xrow(__shfl_sync(kFull, myr, t + 1)), acc);
-        blk_4x1<TV, TX, TA, L>(v + 8, xrow(__shfl_sync(kFull, myr, t + 2)), acc);
-        blk_4x1<TV, TX, TA, L>(v + 12, xrow(__shfl_sync(kFull, myr, t + 3)), acc);
+        Ops::b41(v, xrow(__shfl_sync(kFull, myr, t)), acc);
+        Ops::b41(v + 4, xrow(__shfl_sync(kFull, myr, t + 1)), acc);
+        Ops::b41(v + 8, xrow(__shfl_sync(kFull, myr, t + 2)), acc);
+        Ops::b41(v + 12, xrow(__shfl_sync(kFull, myr, t + 3)), acc);
         v += 16;
       }
       for (; t < cnt; ++t) {
-        blk_4x1<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), acc);
+        Ops::b41(v, xrow(__shfl_sync(kFull, myr, t)), acc);
         v += 4;
       }
     }
@@ -343,13 +448,13 @@ __device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __re
       for (; t + 2 <= cnt; t += 2) {
         const TX* xa = xrow(__shfl_sync(kFull, myr, t));
         const TX* xb = xrow(__shfl_sync(kFull, myr, t + 1));
-        blk_1x4<TV, TX, TA, L>(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
-        blk_1x4<TV, TX, TA, L>(v + 4, xb, xb + W, xb + 2 * W, xb + 3 * W, acc);
+        Ops::b14(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
+        Ops::b14(v + 4, xb, xb + W, xb + 2 * W, xb + 3 * W, acc);
         v += 8;
       }
       if (t < cnt) {
         const TX* xa = xrow(__shfl_sync(kFull, myr, t));
-        blk_1x4<TV, TX, TA, L>(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
+        Ops::b14(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
         v += 4;
       }
     }
@@ -358,7 +463,7 @@ __device__ __forceinline__ void atom_row_product(const Layout& g, const TV* __re
       const int cnt = min(32, e1 - base);
       const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
       for (int t = 0; t < cnt; t += 4) {
-        blk_1x4<TV, TX, TA, L>(v, xrow(__shfl_sync(kFull, myr, t)), xrow(__shfl_sync(kFull, myr, t + 1)),
+        Ops::b14(v, xrow(__shfl_sync(kFull, myr, t)), xrow(__shfl_sync(kFull, myr, t + 1)),
                                xrow(__shfl_sync(kFull, myr, t + 2)), xrow(__shfl_sync(kFull, myr, t + 3)), acc);
         v += 4;
       }
@@ -379,8 +484,10 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
   for (int I = a0 + warp; I < a1; I += kWarps) {
     TA acc[4][L];
     int oI, r0;
-    atom_row_product<TV, TX, TA, L>(a.g, a.val, a.X, W, lane0, I, acc, oI, r0);
-    for (int r = 0; r < oI; ++r) {
+    atom_row_product<PlainOps<TV, TX, TA, L>, L>(a.g, a.val, a.X, W, lane0, I, acc, oI, r0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= oI) break;
       const size_t base = (size_t)(r0 + r) * W + lane0;
       TY y[L];
       if constexpr (MODE == SP_DOT) {
@@ -410,6 +517,78 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
   double d[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) d[i] = double(dot[i]);
+  lane_reduce_commit<L>(d, a.red);
+}
+
+// Double-float SpMM: Y = S X (SP_DOT: X = q in double-float, Y double-float,
+// per-lane dot X.Y) or the refinement residual r = u - S v0 (SP_RESID: X = v0
+// single, u double-float; r rounded to FP32 into Y and P, Z zeroed, r.r).
+template <typename TX>
+struct SpmmDfArgs {
+  Layout g;
+  const float2* val;
+  const TX* X;
+  float2* Y;          // SP_DOT output
+  const float2* U;    // SP_RESID right-hand side
+  float* R;           // SP_RESID residual (FP32)
+  float* P;           // SP_RESID CG direction
+  float* Z;           // SP_RESID CG solution (zeroed)
+  RedArgs red;
+};
+
+template <typename TX, int L, int MODE>
+__global__ void __launch_bounds__(kThreads) k_spmm_df(const SpmmDfArgs<TX> a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const int warp = threadIdx.x >> 5;
+  dfacc dacc[L];
+  float facc[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    acc_zero(dacc[i]);
+    facc[i] = 0.f;
+  }
+  const int a0 = blockIdx.x * a.g.chunk;
+  const int a1 = min(a0 + a.g.chunk, a.g.n_atoms);
+  for (int I = a0 + warp; I < a1; I += kWarps) {
+    dfacc acc[4][L];
+    int oI, r0;
+    atom_row_product<DfOps<TX, L>, L>(a.g, a.val, a.X, W, lane0, I, acc, oI, r0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= oI) break;
+      const size_t base = (size_t)(r0 + r) * W + lane0;
+      if constexpr (MODE == SP_DOT) {
+        float2 y[L], xo[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) y[i] = df_to_float2(acc_value(acc[r][i]));
+        ld_x<float2, L>(reinterpret_cast<const float2*>(a.X) + base, xo);
+        float* yf = reinterpret_cast<float*>(a.Y + base);
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          reinterpret_cast<float2*>(yf)[i] = y[i];
+          acc_fma(dacc[i], xo[i], y[i]);
+        }
+      } else {
+        float2 uu[L];
+        ld_x<float2, L>(a.U + base, uu);
+        float rr[L], zz[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          const df res = df_sub(df_from_float2(uu[i]), acc_value(acc[r][i]));
+          rr[i] = res.hi + res.lo;
+          zz[i] = 0.f;
+          facc[i] = fmaf(rr[i], rr[i], facc[i]);
+        }
+        st_lanes<float, L>(a.R + base, rr);
+        st_lanes<float, L>(a.P + base, rr);
+        st_lanes<float, L>(a.Z + base, zz);
+      }
+    }
+  }
+  double d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = (MODE == SP_DOT) ? df_to_double(acc_value(dacc[i])) : (double)facc[i];
   lane_reduce_commit<L>(d, a.red);
 }
 
@@ -624,6 +803,145 @@ __global__ void __launch_bounds__(kThreads) k_finish(const VecArgs a) {
   }
 }
 
+// ---- double-float Lanczos vectors (mixed mode with FP32-pair refinement) ----
+// K_U (double-float): u = w - alpha Bq - beta Bq_prev, FP32 start of the B-solve, r.r
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_update_df(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const LaneCtl& c = a.red.c;
+  int st[L], jr[L];
+  df al[L], bp[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int l = lane0 + i;
+    st[i] = c.state[l];
+    al[i] = df_from_double(c.alpha[l]);
+    bp[i] = df_from_double(c.beta_prev[l]);
+    jr[i] = (st[i] == LS_SEED) ? a.red.jobs.col_row[c.job[l]] : -1;
+  }
+  const int slot = (*a.step) & 1;
+  const float2* Bq = reinterpret_cast<const float2*>(slot ? a.ring1 : a.ring0);
+  const float2* Bqm = reinterpret_cast<const float2*>(slot ? a.ring0 : a.ring1);
+  float2* u = reinterpret_cast<float2*>(a.u);
+  float* r = static_cast<float*>(a.r);
+  float* p = static_cast<float*>(a.p);
+  float* x = static_cast<float*>(a.x);
+  float acc[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) acc[i] = 0.f;
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    float2 w[L], b1[L], b2[L];
+    ld_x<float2, L>(u + base, w);
+    ld_x<float2, L>(Bq + base, b1);
+    ld_x<float2, L>(Bqm + base, b2);
+    float ut[L], zero[L];
+    float2 uo[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      df uu;
+      if (st[i] == LS_ACTIVE)
+        uu = df_sub(df_sub(df_from_float2(w[i]), df_mul(al[i], df_from_float2(b1[i]))),
+                    df_mul(bp[i], df_from_float2(b2[i])));
+      else if (st[i] == LS_SEED)
+        uu = df{(row == jr[i]) ? 1.f : 0.f, 0.f};
+      else
+        uu = df{0.f, 0.f};
+      uo[i] = df_to_float2(uu);
+      ut[i] = uu.hi;
+      zero[i] = 0.f;
+      acc[i] = fmaf(ut[i], ut[i], acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) u[base + i] = uo[i];
+    st_lanes<float, L>(r + base, ut);
+    st_lanes<float, L>(p + base, ut);
+    st_lanes<float, L>(x + base, zero);
+  }
+  double d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = (double)acc[i];
+  lane_reduce_commit<L>(d, a.red);
+}
+
+// v = v0 + d exactly as a double-float
+template <int L>
+__device__ __forceinline__ void load_v_df(const VecArgs& a, size_t base, df (&v)[L]) {
+  float v0[L], dd[L];
+  ld_lanes<float, L>(static_cast<const float*>(a.x) + base, v0);
+  ld_lanes<float, L>(static_cast<const float*>(a.x2) + base, dd);
+#pragma unroll
+  for (int i = 0; i < L; ++i) v[i] = two_sum(v0[i], dd[i]);
+}
+
+// K_D (double-float): u.v
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_dot_uv_df(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const float2* u = reinterpret_cast<const float2*>(a.u);
+  dfacc acc[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) acc_zero(acc[i]);
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    float2 uu[L];
+    ld_x<float2, L>(u + base, uu);
+    df v[L];
+    load_v_df<L>(a, base, v);
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc_fma(acc[i], uu[i], df_to_float2(v[i]));
+  }
+  double d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = df_to_double(acc_value(acc[i]));
+  lane_reduce_commit<L>(d, a.red);
+}
+
+// K_F (double-float): q = v / beta, Bq_new = u / beta, previous slot cleared on restart
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_finish_df(const VecArgs a) {
+  const int W = a.red.W;
+  const int lane0 = (threadIdx.x & 31) * L;
+  const LaneCtl& c = a.red.c;
+  df ib[L];
+  bool keep[L], zero_out[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int l = lane0 + i;
+    const double b = c.inv_beta[l];
+    ib[i] = df_from_double(b);
+    zero_out[i] = (b == 0.0);
+    keep[i] = (c.state[l] == LS_ACTIVE && c.n[l] >= 1 && b != 0.0);
+  }
+  const int slot = (*a.step) & 1;
+  float2* Bq_new = reinterpret_cast<float2*>(slot ? a.ring1 : a.ring0);
+  float2* Bq_old = reinterpret_cast<float2*>(slot ? a.ring0 : a.ring1);
+  const float2* u = reinterpret_cast<const float2*>(a.u);
+  float2* q = reinterpret_cast<float2*>(a.q);
+  bool any_clear = false;
+#pragma unroll
+  for (int i = 0; i < L; ++i) any_clear |= !keep[i];
+  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
+    const size_t base = (size_t)row * W + lane0;
+    float2 uu[L];
+    ld_x<float2, L>(u + base, uu);
+    df v[L];
+    load_v_df<L>(a, base, v);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      q[base + i] = zero_out[i] ? make_float2(0.f, 0.f) : df_to_float2(df_mul(v[i], ib[i]));
+      Bq_new[base + i] = zero_out[i] ? make_float2(0.f, 0.f) : df_to_float2(df_mul(df_from_float2(uu[i]), ib[i]));
+    }
+    if (any_clear) {
+#pragma unroll
+      for (int i = 0; i < L; ++i)
+        if (!keep[i]) Bq_old[base + i] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
 // ===========================================================================
 // K4: per-shift recurrences on the pattern rows of each lane's column
 // ===========================================================================
@@ -639,7 +957,8 @@ struct ShiftArgs {
   double2* pbuf;            // [W][Pmax][S]
   double2* xbuf;            // [W][Pmax][S]
   double2* dg;              // [W][2][S][2]  (d, g) per step parity
-  const double* q;          // FP64 q_n (M x W)
+  const double* q;          // q_n (M x W): FP64, or double-float pairs when q_df
+  int q_df;
   double2* G;               // output, job_off layout x S
   int32_t* out_iters;
   int32_t* out_status;
@@ -727,7 +1046,14 @@ __global__ void __launch_bounds__(kThreads) k_shift(const ShiftArgs a) {
     const size_t e = (size_t)i * S + k;
     double2 xv;
     if (!bad) {
-      const double qi = a.q[(size_t)a.prow[off + i] * a.W + lane];
+      const size_t qidx = (size_t)a.prow[off + i] * a.W + lane;
+      double qi;
+      if (a.q_df) {
+        const float2 qq = reinterpret_cast<const float2*>(a.q)[qidx];
+        qi = (double)qq.x + (double)qq.y;
+      } else {
+        qi = a.q[qidx];
+      }
       double2 pv;
       if (n == 1) {
         pv = make_double2(qi, 0.0);
@@ -867,13 +1193,13 @@ struct GraphBuilder {
   explicit GraphBuilder(cudaGraph_t graph) : g(graph) {}
 
   template <typename A>
-  void kernel(void (*f)(A), dim3 grid, dim3 block, const A& arg) {
+  void kernel(void (*f)(A), dim3 grid, dim3 block, const A& arg, unsigned smem = 0) {
     if (err != cudaSuccess) return;
     cudaKernelNodeParams p = {};
     p.func = reinterpret_cast<void*>(f);
     p.gridDim = grid;
     p.blockDim = block;
-    p.sharedMemBytes = 0;
+    p.sharedMemBytes = smem;
     void* args[1] = {const_cast<A*>(&arg)};
     p.kernelParams = args;
     p.extra = nullptr;
@@ -907,6 +1233,7 @@ struct Plan {
   int W = 64;
   int L = 2;
   bool mixed = false;
+  bool df = false;       // mixed mode with double-float refinement / Lanczos vectors
   bool refine = true;
   int grid_rows = 1;     // SpMM CTAs (== lay.n_ctas)
   int grid_vec = 1;      // vector-kernel CTAs
@@ -916,6 +1243,8 @@ struct Plan {
   SpmmArgs<double, double, double> spB64;
   SpmmArgs<float, float, float> spB32[2];
   SpmmArgs<double, float, float> spR;
+  SpmmDfArgs<float2> spAdf;
+  SpmmDfArgs<float> spRdf;
   VecArgs upd, cgu[2], cgp[2], dot, fin;
   ShiftArgs sh;
   PrimeArgs prime;
@@ -939,6 +1268,12 @@ struct Kernels {
   static constexpr auto cgp32 = k_cg_dir<float, L>;
   static constexpr auto dotm = k_dot_uv<float, L, true>;
   static constexpr auto finm = k_finish<float, L, true>;
+  // mixed mode, double-float refinement
+  static constexpr auto spmm_df = k_spmm_df<float2, L, SP_DOT>;
+  static constexpr auto resid_df = k_spmm_df<float, L, SP_RESID>;
+  static constexpr auto upd_df = k_update_df<L>;
+  static constexpr auto dot_df = k_dot_uv_df<L>;
+  static constexpr auto fin_df = k_finish_df<L>;
 };
 
 // Launch of one kernel either into a graph (builder) or onto a stream.
@@ -946,26 +1281,36 @@ struct Launcher {
   GraphBuilder* gb = nullptr;
   cudaStream_t stream = nullptr;
   template <typename A>
-  cudaError_t operator()(void (*f)(A), dim3 grid, dim3 block, const A& arg) {
+  cudaError_t operator()(void (*f)(A), dim3 grid, dim3 block, const A& arg, unsigned smem = 0) {
     if (gb) {
-      gb->kernel(f, grid, block, arg);
+      gb->kernel(f, grid, block, arg, smem);
       return gb->err;
     }
-    f<<<grid, block, 0, stream>>>(arg);
+    f<<<grid, block, smem, stream>>>(arg);
     return cudaGetLastError();
   }
 };
+
+// Dynamic shared memory of the SpMM kernels (none: the traversal keeps its
+// neighbour blocks in registers and the L1 cache).
+template <typename TV, typename TX, int L>
+constexpr unsigned spmm_smem() { return 0u; }
+template <typename A>
+cudaError_t allow_smem(void (*f)(A), unsigned bytes) {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
+}
 
 template <int L>
 cudaError_t launch_cg_iteration(const Plan& P, Launcher& la, int pass) {
   using K = Kernels<L>;
   const dim3 blk(kThreads);
   if (!P.mixed) {
-    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spB64));
+    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spB64, spmm_smem<double, double, L>()));
     GSK_CUDA_TRY(la(K::cgu64, dim3(P.grid_vec), blk, P.cgu[0]));
     GSK_CUDA_TRY(la(K::cgp64, dim3(P.grid_vec), blk, P.cgp[0]));
   } else {
-    GSK_CUDA_TRY(la(K::spmm32, dim3(P.grid_rows), blk, P.spB32[pass]));
+    GSK_CUDA_TRY(la(K::spmm32, dim3(P.grid_rows), blk, P.spB32[pass], spmm_smem<float, float, L>()));
     GSK_CUDA_TRY(la(K::cgu32, dim3(P.grid_vec), blk, P.cgu[pass]));
     GSK_CUDA_TRY(la(K::cgp32, dim3(P.grid_vec), blk, P.cgp[pass]));
   }
@@ -976,11 +1321,16 @@ template <int L>
 cudaError_t launch_step_head(const Plan& P, Launcher& la) {
   using K = Kernels<L>;
   const dim3 blk(kThreads);
-  GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spA));
-  if (!P.mixed)
-    GSK_CUDA_TRY(la(K::upd64, dim3(P.grid_vec), blk, P.upd));
-  else
-    GSK_CUDA_TRY(la(K::upd32, dim3(P.grid_vec), blk, P.upd));
+  if (P.df) {
+    GSK_CUDA_TRY(la(K::spmm_df, dim3(P.grid_rows), blk, P.spAdf, spmm_smem<float2, float2, L>()));
+    GSK_CUDA_TRY(la(K::upd_df, dim3(P.grid_vec), blk, P.upd));
+  } else {
+    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spA, spmm_smem<double, double, L>()));
+    if (!P.mixed)
+      GSK_CUDA_TRY(la(K::upd64, dim3(P.grid_vec), blk, P.upd));
+    else
+      GSK_CUDA_TRY(la(K::upd32, dim3(P.grid_vec), blk, P.upd));
+  }
   GSK_CUDA_TRY(la(k_shift, dim3(P.W, P.nsplit), blk, P.sh));
   return cudaSuccess;
 }
@@ -989,7 +1339,10 @@ template <int L>
 cudaError_t launch_step_tail(const Plan& P, Launcher& la) {
   using K = Kernels<L>;
   const dim3 blk(kThreads);
-  if (!P.mixed) {
+  if (P.df) {
+    GSK_CUDA_TRY(la(K::dot_df, dim3(P.grid_vec), blk, P.dot));
+    GSK_CUDA_TRY(la(K::fin_df, dim3(P.grid_vec), blk, P.fin));
+  } else if (!P.mixed) {
     GSK_CUDA_TRY(la(K::dot64, dim3(P.grid_vec), blk, P.dot));
     GSK_CUDA_TRY(la(K::fin64, dim3(P.grid_vec), blk, P.fin));
   } else {
@@ -1002,7 +1355,19 @@ cudaError_t launch_step_tail(const Plan& P, Launcher& la) {
 template <int L>
 cudaError_t launch_resid(const Plan& P, Launcher& la) {
   using K = Kernels<L>;
-  return la(K::resid, dim3(P.grid_rows), dim3(kThreads), P.spR);
+  if (P.df) return la(K::resid_df, dim3(P.grid_rows), dim3(kThreads), P.spRdf, spmm_smem<float2, float, L>());
+  return la(K::resid, dim3(P.grid_rows), dim3(kThreads), P.spR, spmm_smem<double, float, L>());
+}
+
+template <int L>
+cudaError_t allow_spmm_smem() {
+  using K = Kernels<L>;
+  GSK_CUDA_TRY(allow_smem(K::spmm64, spmm_smem<double, double, L>()));
+  GSK_CUDA_TRY(allow_smem(K::spmm32, spmm_smem<float, float, L>()));
+  GSK_CUDA_TRY(allow_smem(K::resid, spmm_smem<double, float, L>()));
+  GSK_CUDA_TRY(allow_smem(K::spmm_df, spmm_smem<float2, float2, L>()));
+  GSK_CUDA_TRY(allow_smem(K::resid_df, spmm_smem<float2, float, L>()));
+  return cudaSuccess;
 }
 
 // Builds the whole solve as one graph: prime -> WHILE(outer) { head, WHILE(cg1),
@@ -1039,6 +1404,7 @@ cudaError_t build_graph(Plan& P, cudaGraphExec_t* exec) {
     gc.h_inner2 = h_in2;
     // propagate graph control into every argument block
     RedArgs* reds[] = {&P.spA.red, &P.spB64.red, &P.spB32[0].red, &P.spB32[1].red, &P.spR.red,
+                       &P.spAdf.red, &P.spRdf.red,
                        &P.upd.red, &P.cgu[0].red, &P.cgu[1].red, &P.cgp[0].red, &P.cgp[1].red,
                        &P.dot.red, &P.fin.red};
     for (RedArgs* r : reds) r->gc = gc;
@@ -1122,7 +1488,8 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   if (opt_in) opt = *opt_in;
   if (S < 1 || S > kMaxShifts || n_cols < 0 || !z || (n_cols > 0 && (!cols || !G_out)))
     return GSK_EINVAL;
-  if (opt.precision != GSK_FP64 && opt.precision != GSK_MIXED) return GSK_EINVAL;
+  if (opt.precision != GSK_FP64 && opt.precision != GSK_MIXED && opt.precision != GSK_MIXED_DF)
+    return GSK_EINVAL;
   if (!(opt.tol > 0.0) || opt.max_iter < 1) return GSK_EINVAL;
   if (opt.batch_w != 0 && opt.batch_w != 32 && opt.batch_w != 64 && opt.batch_w != 128) return GSK_EINVAL;
   if (opt.precision == GSK_FP64 && opt.batch_w == 128) return GSK_ENOTSUP;
@@ -1146,7 +1513,8 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   cudaStream_t stream = static_cast<cudaStream_t>(opt.stream);
 
   Plan P;
-  P.mixed = (opt.precision == GSK_MIXED);
+  P.mixed = (opt.precision != GSK_FP64);
+  P.df = (opt.precision == GSK_MIXED_DF);
   P.refine = P.mixed && opt.refine != 0;
   int W = opt.batch_w;
   if (W == 0) {
@@ -1174,10 +1542,16 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   for (int c = 0; c < n_cols; ++c) {
     const int j = cols[c];
     col_row[c] = h->row_lib[j];
-    jeta[c] = eta ? eta[c] : 0.0;
+    jeta[c] = eta ? eta[c] : z[1];
     int64_t t = job_off[c];
     for (int64_t e = h->row_ptr[j]; e < h->row_ptr[j + 1]; ++e) prow[t++] = h->row_lib[h->col_idx[e]];
     queue[c] = c;
+  }
+  if (opt.sched == GSK_SCHED_LEARNED) {
+    const int rc = learned_order(h, n_cols, cols, jeta.data(), stream, queue);
+    if (rc != GSK_OK) return rc;
+  } else if (opt.sched != GSK_SCHED_FIFO) {
+    return GSK_EINVAL;
   }
   std::vector<double> eps(2 * S);
   for (int k = 0; k < S; ++k) {
@@ -1313,6 +1687,10 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   for (int ps = 0; ps < 2; ++ps)
     P.spB32[ps] = {g, h->d_B32.as<float>(), static_cast<float*>(p), static_cast<float*>(Bp), nullptr, nullptr, nullptr, red(FIN_CG_A)};
   P.spR = {g, h->d_B64.as<double>(), static_cast<float*>(x), static_cast<float*>(r), u, static_cast<float*>(p), static_cast<float*>(x2), red(FIN_RESID)};
+  P.spAdf = {g, h->d_A2.as<float2>(), reinterpret_cast<const float2*>(q), reinterpret_cast<float2*>(u), nullptr,
+             nullptr, nullptr, nullptr, red(FIN_ALPHA)};
+  P.spRdf = {g, h->d_B2.as<float2>(), static_cast<const float*>(x), nullptr, reinterpret_cast<const float2*>(u),
+             static_cast<float*>(r), static_cast<float*>(p), static_cast<float*>(x2), red(FIN_RESID)};
   VecArgs va{};
   va.M = M; va.q = q; va.ring0 = ring0; va.ring1 = ring1; va.u = u;
   va.r = r; va.p = p; va.Bp = Bp; va.x = x; va.x2 = x2; va.step = c.step;
@@ -1328,7 +1706,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   P.dot = va; P.dot.red = red(FIN_BETA);
   P.fin = va; P.fin.red = red(FIN_SUM);
   P.nsplit = std::max(1, std::min(8, (h->num_sms * 2) / W));
-  P.sh = ShiftArgs{c, jobs, W, S, Pmax, P.nsplit, d_eps, d_eps + S, eta ? 1 : 0, d_job_off, d_prow, pbuf, xbuf, dgb, q, Gd,
+  P.sh = ShiftArgs{c, jobs, W, S, Pmax, P.nsplit, d_eps, d_eps + S, eta ? 1 : 0, d_job_off, d_prow, pbuf, xbuf, dgb, q, P.df ? 1 : 0, Gd,
                    d_iters, d_status, d_resid, opt.tol, opt.max_iter};
   P.prime = PrimeArgs{c, jobs, gc, W};
   P.wrap = WrapArgs{c, jobs, W, S, Pmax, d_job_off, xbuf, Gd, d_iters, d_status, d_resid};
@@ -1336,6 +1714,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   // ---- run ----
   auto run = [&](auto Ltag) -> cudaError_t {
     constexpr int LL = decltype(Ltag)::value;
+    GSK_CUDA_TRY(allow_spmm_smem<LL>());
     if (opt.use_graph) {
       cudaGraphExec_t ex = nullptr;
       cudaError_t ge = build_graph<LL>(P, &ex);
@@ -1429,15 +1808,27 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
       SpmmArgs<double, double, double> a{h->lay, (which ? h->d_B64 : h->d_A64).as<double>(),
                                          static_cast<const double*>(X), static_cast<double*>(Y),
                                          nullptr, nullptr, nullptr, r};
-      if (W == 32) k_spmm<double, double, double, double, 1, SP_DOT><<<grd, blk, 0, s>>>(a);
-      else k_spmm<double, double, double, double, 2, SP_DOT><<<grd, blk, 0, s>>>(a);
+      if (W == 32) {
+        allow_smem(k_spmm<double, double, double, double, 1, SP_DOT>, spmm_smem<double, double, 1>());
+        k_spmm<double, double, double, double, 1, SP_DOT><<<grd, blk, spmm_smem<double, double, 1>(), s>>>(a);
+      } else {
+        allow_smem(k_spmm<double, double, double, double, 2, SP_DOT>, spmm_smem<double, double, 2>());
+        k_spmm<double, double, double, double, 2, SP_DOT><<<grd, blk, spmm_smem<double, double, 2>(), s>>>(a);
+      }
     } else {
       SpmmArgs<float, float, float> a{h->lay, (which ? h->d_B32 : h->d_A32).as<float>(),
                                       static_cast<const float*>(X), static_cast<float*>(Y),
                                       nullptr, nullptr, nullptr, r};
-      if (W == 32) k_spmm<float, float, float, float, 1, SP_DOT><<<grd, blk, 0, s>>>(a);
-      else if (W == 64) k_spmm<float, float, float, float, 2, SP_DOT><<<grd, blk, 0, s>>>(a);
-      else k_spmm<float, float, float, float, 4, SP_DOT><<<grd, blk, 0, s>>>(a);
+      if (W == 32) {
+        allow_smem(k_spmm<float, float, float, float, 1, SP_DOT>, spmm_smem<float, float, 1>());
+        k_spmm<float, float, float, float, 1, SP_DOT><<<grd, blk, spmm_smem<float, float, 1>(), s>>>(a);
+      } else if (W == 64) {
+        allow_smem(k_spmm<float, float, float, float, 2, SP_DOT>, spmm_smem<float, float, 2>());
+        k_spmm<float, float, float, float, 2, SP_DOT><<<grd, blk, spmm_smem<float, float, 2>(), s>>>(a);
+      } else {
+        allow_smem(k_spmm<float, float, float, float, 4, SP_DOT>, spmm_smem<float, float, 4>());
+        k_spmm<float, float, float, float, 4, SP_DOT><<<grd, blk, spmm_smem<float, float, 4>(), s>>>(a);
+      }
     }
     if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
   }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libgsk.so")
 
 GSK_OK, GSK_EINVAL, GSK_ENOTSPD, GSK_ENOMEM, GSK_ECUDA, GSK_ETIMEOUT, GSK_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 GSK_CONVERGED, GSK_NOT_CONVERGED, GSK_BREAKDOWN, GSK_TIMEOUT = 0, 1, 2, 3
-GSK_FP64, GSK_MIXED = 0, 1
+GSK_FP64, GSK_MIXED, GSK_MIXED_DF = 0, 1, 2
 GSK_SCHED_FIFO, GSK_SCHED_LEARNED = 0, 1
 
 
@@ -67,6 +67,11 @@ def _load() -> C.CDLL:
         "gsk_row_order": (C.c_int, [P, P]),
         "gsk_spmm": (C.c_int, [P, I32, I32, I32, P, P, I32, P]),
         "gsk_density_noalloc": (C.c_int, [I64, I32, P, P, D, D, P, P, P]),
+        "gsk_features": (C.c_int, [P, I32, P, P, P, P]),
+        "gsk_mlp_forward": (C.c_int, [I32, P, P, P, P, P]),
+        "gsk_mlp_workspace_bytes": (C.c_size_t, [I32]),
+        "gsk_mlp_train_step": (C.c_int, [I32, P, P, P, P, P, P, I32, C.c_float, P, P, P, P]),
+        "gsk_set_sched_model": (C.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -103,7 +108,7 @@ def _ptr(a) -> int:
 def default_options(**kw) -> Options:
     o = Options()
     _lib.gsk_default_options(C.byref(o))
-    names = {"precision": {"fp64": GSK_FP64, "mixed": GSK_MIXED},
+    names = {"precision": {"fp64": GSK_FP64, "mixed": GSK_MIXED, "mixed_df": GSK_MIXED_DF},
              "sched": {"fifo": GSK_SCHED_FIFO, "learned": GSK_SCHED_LEARNED}}
     for k, v in kw.items():
         if v is None:
@@ -166,6 +171,17 @@ class Solver:
         _check(_lib.gsk_last_stats(self._h, C.byref(st)), "gsk_last_stats")
         return {k: getattr(st, k) for k, _ in Stats._fields_}
 
+    def features(self, cols, eta, feat) -> None:
+        """Scheduler features of the columns into feat (device tensor, n x 16 float32)."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        _check(_lib.gsk_features(self._h, cols.size, _ptr(cols), _ptr(eta), _ptr(feat), None), "gsk_features")
+
+    def set_sched_model(self, params, norm) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        nm = np.ascontiguousarray(norm, dtype=np.float32)
+        _check(_lib.gsk_set_sched_model(self._h, _ptr(p), _ptr(nm)), "gsk_set_sched_model")
+
     def row_order(self) -> np.ndarray:
         out = np.empty(self.M, dtype=np.int32)
         _check(_lib.gsk_row_order(self._h, _ptr(out)), "gsk_row_order")
@@ -222,6 +238,25 @@ def density_noalloc(G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=No
     s = getattr(stream, "cuda_stream", stream)
     _check(_lib.gsk_density_noalloc(int(n_elem), eps.size, _ptr(eps), _ptr(w), float(mu), float(kT),
                                     _ptr(G), _ptr(rho), s), "gsk_density_noalloc")
+
+
+MLP_IN, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
+
+
+def mlp_forward(n: int, feat, norm, params, y, stream=None) -> None:
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_lib.gsk_mlp_forward(int(n), _ptr(feat), _ptr(norm), _ptr(params), _ptr(y), s), "gsk_mlp_forward")
+
+
+def mlp_workspace_bytes(n: int) -> int:
+    return int(_lib.gsk_mlp_workspace_bytes(int(n)))
+
+
+def mlp_train_step(n: int, feat, norm, target, params, m, v, t: int, lr: float, work, grad=None, loss=None,
+                   stream=None) -> None:
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_lib.gsk_mlp_train_step(int(n), _ptr(feat), _ptr(norm), _ptr(target), _ptr(params), _ptr(m), _ptr(v),
+                                   int(t), float(lr), _ptr(grad), _ptr(loss), _ptr(work), s), "gsk_mlp_train_step")
 
 
 def from_system(sys_, pos=True) -> Solver:

@@ -74,11 +74,12 @@ def test_graph_and_host_loop_identical(gsk, c64, c64_ref):
     assert np.array_equal(Ga, Gb)
 
 
-@pytest.mark.parametrize("W", [32, 64, 128])
-def test_c64_mixed_refined(gsk, c64, c64_ref, W):
+@pytest.mark.parametrize("prec,W", [("mixed", 32), ("mixed", 64), ("mixed", 128), ("mixed_df", 64),
+                                    ("mixed_df", 128)])
+def test_c64_mixed_refined(gsk, c64, c64_ref, prec, W):
     eps, z, cols, G1 = c64_ref
     s = gsk.from_system(c64)
-    G, it, st, rs = _run(gsk, s, z, cols, precision="mixed", refine=1, tol=1e-10, batch_w=W)
+    G, it, st, rs = _run(gsk, s, z, cols, precision=prec, refine=1, tol=1e-10, batch_w=W)
     assert (st == gsk.GSK_CONVERGED).all()
     assert _rel(G, G1) <= 1e-8
 
@@ -201,7 +202,7 @@ def test_ch1k_fp64_and_mixed_subset(gsk, ch1k):
     cols = np.unique(np.concatenate([np.arange(0, ch1k.M, 97), [ch1k.M - 1]]))
     R = dense.green_lu(ch1k.A, ch1k.B, z, cols)
     s = gsk.from_system(ch1k)
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_df"):
         G, it, st, _ = _run(gsk, s, z, cols, precision=prec, tol=1e-10)
         assert (st == gsk.GSK_CONVERGED).all()
         assert _rel(G, R) <= 1e-8, prec
