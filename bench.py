@@ -42,9 +42,9 @@ def _parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ch20k")
     ap.add_argument("--cols-per-step", type=int, default=128)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
     ap.add_argument("--batch-w", type=int, default=0)
-    ap.add_argument("--sched", default="fifo", choices=["fifo", "learned"])
+    ap.add_argument("--sched", default="learned", choices=["fifo", "learned"])
     ap.add_argument("--no-graph", action="store_true", help="host-driven loop (for kernel-level profiling)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
@@ -69,6 +69,40 @@ def make_workload(name: str, seed: int):
     else:
         eta = np.full(cols.size, wl.eta)
     return wl, sys_, eps, cols, eta
+
+
+def workload_config(wl, sys_, S: int, C: int, args, world: int) -> dict:
+    """The workload description shared by both arms of the benchmark."""
+    return {"workload": f"{wl.name}: {sys_.n_atoms} atoms (1/3 C 4-orbital, 2/3 H 1-orbital), "
+                        f"M={sys_.M}, nnz={sys_.nnz}, {S} shifts on [-25,5] eV, eta per column in "
+                        f"{{0.05,0.1,0.2}} eV, {C} seeded columns per step",
+            "cols_per_step": C, "n_shifts": S, "tol": 1e-8, "precision": args.precision,
+            "sched": args.sched, "graph": not args.no_graph, "l2": "flushed between steps (256 MB write)",
+            "parallelism": f"columns sharded over {world} rank(s)"}
+
+
+def rank_batches(n_cols: int, C: int, n_batches: int, rank: int, world: int):
+    """Column ranges [a, b) of this rank's batches: batch b of rank r is block
+    (b * world + r) of C consecutive columns of the (shuffled) column set, so
+    ranks never share a column within a run (weak scaling: every rank solves
+    n_batches blocks of C columns)."""
+    n_blocks = max(1, n_cols // C)
+    out = []
+    for b in range(n_batches):
+        k = (b * world + rank) % n_blocks
+        out.append((k * C, min(n_cols, (k + 1) * C)))
+    return out
+
+
+def max_over_ranks(t_local: float, dist=None, device=None) -> float:
+    """Step time of the job: the slowest rank's time."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t_local
+    import torch
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------------------
@@ -189,13 +223,12 @@ def main():
     S = eps.size
     z = eps.astype(np.complex128) + 1j * 1.0        # real parts; damping per column via eta
     solver = gsk.from_system(sys_)
+    if args.sched == "learned":
+        from paper_1609_08377_gb300 import scheduler
+        scheduler.install(solver, scheduler.load())
     C = args.cols_per_step
     n_batches = args.warmup + args.steps + 1
-    # rank r takes batches r, r + world, ... (disjoint columns per rank)
-    batches = []
-    for b in range(n_batches):
-        k = (b * world + rank) % max(1, cols_all.size // C)
-        batches.append((cols_all[k * C:(k + 1) * C], eta_all[k * C:(k + 1) * C]))
+    batches = [(cols_all[a:b], eta_all[a:b]) for a, b in rank_batches(cols_all.size, C, n_batches, rank, world)]
     max_elem = max(int(solver.pattern_offsets(c)[-1]) for c, _ in batches)
     G = torch.empty(max_elem * S, dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -206,6 +239,12 @@ def main():
     def step(b, Gbuf):
         c, e = batches[b]
         return solver.solve(z, c, Gbuf, eta=e, **opts)
+
+    # lane width: autotuned on the first batch (setup, untimed) unless given
+    tuned_w = args.batch_w
+    if args.batch_w == 0:
+        tuned_w = solver.autotune(z, batches[0][0], eta=batches[0][1], precision=args.precision,
+                                  stream=stream.cuda_stream)
 
     for b in range(args.warmup):
         flush.zero_()
@@ -236,12 +275,7 @@ def main():
         status_all.append(st)
     clock = clocks.stop()
     t_local = float(np.sum(times))
-    if dist is not None:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    else:
-        t_total = t_local
+    t_total = max_over_ranks(t_local, dist, dev)
     solves = args.steps * C * S * world
     value = solves / (t_total / 1e3)
     iters_all = np.concatenate(iters_all)
@@ -269,15 +303,11 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed_df": "f32+f32x2+f64", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded C/H tight-binding-like pencil standing in for the paper's PPE structures)",
-        "config": {"workload": f"{wl.name}: {sys_.n_atoms} atoms (1/3 C 4-orbital, 2/3 H 1-orbital), "
-                               f"M={sys_.M}, nnz={sys_.nnz}, {S} shifts on [-25,5] eV, eta per column in "
-                               f"{{0.05,0.1,0.2}} eV, {C} seeded columns per step",
-                   "cols_per_step": C, "n_shifts": S, "tol": 1e-8, "precision": args.precision,
-                   "sched": args.sched, "batch_w": int(solver.last_stats()["batch_w"]),
-                   "graph": not args.no_graph, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"columns sharded over {world} rank(s)"},
+        "config": workload_config(wl, sys_, S, C, args, world),
+        "batch_w": int(solver.last_stats()["batch_w"]), "batch_w_autotuned": args.batch_w == 0,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -301,7 +331,7 @@ def spmm_roofline(solver, sys_, args, stream, dev) -> dict:
     from paper_1609_08377_gb300 import gsk
 
     W = int(solver.last_stats()["batch_w"]) or 64
-    prec = gsk.GSK_MIXED if args.precision == "mixed" else gsk.GSK_FP64
+    prec = gsk.GSK_FP64 if args.precision == "fp64" else gsk.GSK_MIXED
     dt = torch.float32 if prec == gsk.GSK_MIXED else torch.float64
     M = sys_.M
     X = torch.randn(M * W, dtype=dt, device=dev)
@@ -395,7 +425,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": wl.name, "n_shifts": S},
+           "data": "synthetic (seeded C/H tight-binding-like pencil standing in for the paper's PPE structures)",
+           "config": workload_config(wl, sys_, S, args.cols_per_step, args, 1),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{steps_budget} Lanczos steps of one column per step, scaled by "
                                       f"{mean_iters:.0f} steps per column ({src})"},

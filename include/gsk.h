@@ -250,6 +250,18 @@ int gsk_mlp_train_step(int32_t n, const float* feat, const float* norm, const fl
 /* Install a trained model (host arrays) on the handle for GSK_SCHED_LEARNED. */
 int gsk_set_sched_model(gsk_handle h, const float* params, const float* norm);
 
+/* Autotuner of the lane width W (columns in flight). For each candidate W
+ * (32, 64 and, in the mixed modes, 128) it times, with CUDA events, a
+ * truncated solve (a few Lanczos steps) of the first columns of the set and
+ * picks the W that minimises the estimated time of the whole set,
+ * t_step(W) * max(n_cols / W, 2) in units of a column's mean step count (the
+ * factor 2 accounts for the longest column of a set with mixed damping). The
+ * result is cached on the handle for opt->precision and used by gsk_solve
+ * whenever opt->batch_w is 0. Arguments as for gsk_solve; *best_w receives the
+ * choice (host). Synchronous. */
+int gsk_autotune(gsk_handle h, int32_t n_shifts, const double* z, const double* eta, int32_t n_cols,
+                 const int32_t* cols, const gsk_options* opt, int32_t* best_w);
+
 /* Counters of the last gsk_solve on this handle. */
 typedef struct {
   int64_t outer_steps;       /* Lanczos steps of the lane batch (lock-step) */

@@ -436,6 +436,34 @@ int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_ha
   L.M = M;
   L.n_ctas = std::max(1, std::min((N + gsk::kWarps - 1) / gsk::kWarps, h->num_sms * 6));
   L.chunk = (N + L.n_ctas - 1) / L.n_ctas;
+  // Static balance of the SpMM traversal: the atoms are cut into one
+  // contiguous segment per warp of about equal cost, the cost of an atom being
+  // its multiply-adds per lane plus a load overhead per neighbour block. The
+  // cut is fixed at creation, so every product sums in the same order.
+  {
+    const int n_w = L.n_ctas * gsk::kWarps;
+    std::vector<double> cost(N);
+    double total = 0.0;
+    for (int32_t I = 0; I < N; ++I) {
+      const int n4 = nbr_mid[I] - nbr_ptr[I];
+      const int n1 = nbr_ptr[I + 1] - nbr_mid[I];
+      const double fma = (double)orb[I] * (4.0 * n4 + n1);
+      const double blocks = (orb[I] == 4) ? (double)(n4 + n1) : (double)n4 + n1 / 4.0;
+      cost[I] = fma + 8.0 * blocks;
+      total += cost[I];
+    }
+    std::vector<int32_t> cut(n_w + 1, N);
+    cut[0] = 0;
+    double acc = 0.0;
+    int w = 1;
+    for (int32_t I = 0; I < N && w < n_w; ++I) {
+      acc += cost[I];
+      while (w < n_w && acc >= total * w / n_w) cut[w++] = I + 1;
+    }
+    for (; w < n_w; ++w) cut[w] = N;
+    if (upload(h->d_warp_atoms, cut) != cudaSuccess) return fail(GSK_ECUDA);
+    L.warp_atoms = h->d_warp_atoms.as<int32_t>();
+  }
   L.atom_roff = h->d_atom_roff.as<int32_t>();
   L.atom_orb = h->d_atom_orb.as<int8_t>();
   L.nbr_ptr = h->d_nbr_ptr.as<int32_t>();
@@ -456,6 +484,12 @@ int gsk_destroy(gsk_handle h) {
   delete h;
   if (dev >= 0) cudaSetDevice(dev);
   return GSK_OK;
+}
+
+int gsk_autotune(gsk_handle h, int32_t n_shifts, const double* z, const double* eta, int32_t n_cols,
+                 const int32_t* cols, const gsk_options* opt, int32_t* best_w) {
+  if (!h) return GSK_EINVAL;
+  return gsk::autotune_impl(h, n_shifts, z, eta, n_cols, cols, opt, best_w);
 }
 
 int gsk_row_order(gsk_handle h, int32_t* row_lib) {

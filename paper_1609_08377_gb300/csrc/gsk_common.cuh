@@ -40,6 +40,7 @@ struct Layout {
   const int32_t* nbr_mid;        // n_atoms
   const int32_t* nbr_roff;       // neighbour entries
   const int64_t* val_ptr;        // n_atoms
+  const int32_t* warp_atoms;     // n_ctas * kWarps + 1: atoms [warp_atoms[w], warp_atoms[w+1]) of warp w
 };
 
 // Lane states of the batched solver.
@@ -236,15 +237,19 @@ __device__ __forceinline__ double fold_rows(const double* __restrict__ src, int 
 // per-lane partial; the last CTA to arrive in each group of kRedGroup CTAs
 // folds the group (fixed order); the last group to arrive folds the group
 // sums and runs the finalisation. Counters are reset by their last user.
+// mine[i] is this thread's partial for lane lane0 + i; within a warp the
+// threads with writer = true cover every lane exactly once.
 template <int L>
-__device__ __forceinline__ void lane_reduce_commit(const double (&mine)[L], const RedArgs& r) {
+__device__ __forceinline__ void lane_reduce_commit_at(const double (&mine)[L], const RedArgs& r, int lane0,
+                                                      bool writer) {
   __shared__ double sm[kWarps][kMaxW];
   __shared__ bool is_last;
   const int W = r.W;
   const int warp = threadIdx.x >> 5;
-  const int lane0 = (threadIdx.x & 31) * L;
+  if (writer) {
 #pragma unroll
-  for (int i = 0; i < L; ++i) sm[warp][lane0 + i] = mine[i];
+    for (int i = 0; i < L; ++i) sm[warp][lane0 + i] = mine[i];
+  }
   __syncthreads();
   if (threadIdx.x < W) {
     double s = 0.0;
@@ -284,6 +289,11 @@ __device__ __forceinline__ void lane_reduce_commit(const double (&mine)[L], cons
     finalize_all(r);
     *r.c.red_counter = 0u;
   }
+}
+
+template <int L>
+__device__ __forceinline__ void lane_reduce_commit(const double (&mine)[L], const RedArgs& r) {
+  lane_reduce_commit_at<L>(mine, r, (threadIdx.x & 31) * L, true);
 }
 
 }  // namespace gsk

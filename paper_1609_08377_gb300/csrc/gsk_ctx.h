@@ -55,7 +55,7 @@ struct gsk_ctx {
 
   // device block layout
   gsk::Layout lay{};
-  gsk::DevBuf d_atom_roff, d_atom_orb, d_nbr_ptr, d_nbr_mid, d_nbr_roff, d_val_ptr;
+  gsk::DevBuf d_atom_roff, d_atom_orb, d_nbr_ptr, d_nbr_mid, d_nbr_roff, d_val_ptr, d_warp_atoms;
   gsk::DevBuf d_A64, d_B64, d_A32, d_B32, d_A2, d_B2;   // FP64, FP32, FP32 pairs (hi, lo)
 
   gsk_stats last{};
@@ -67,6 +67,9 @@ struct gsk_ctx {
   gsk::DevBuf ws_sched;           // feature / prediction scratch
   bool sched_ready = false;
 
+  // autotuned lane width per precision mode (0: not tuned)
+  int tuned_w[3] = {0, 0, 0};
+
   // solver workspace (grown on demand)
   gsk::DevBuf ws_vec;      // Lanczos / CG vectors
   gsk::DevBuf ws_lane;     // lane control block
@@ -74,11 +77,12 @@ struct gsk_ctx {
   gsk::DevBuf ws_shift;    // shift recurrence state
   gsk::DevBuf ws_gstage;   // staging of G for host output buffers
   gsk::DevBuf ws_misc;     // density / trace scratch
+  gsk::DevBuf ws_tune;     // G of the autotuner's truncated solves
 
   ~gsk_ctx() {
-    gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr,
+    gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr, &d_warp_atoms,
                           &d_A64, &d_B64, &d_A32, &d_B32, &d_A2, &d_B2, &ws_vec, &ws_lane, &ws_jobs,
-                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched};
+                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune};
     for (auto* b : all) b->release();
   }
 };
@@ -91,6 +95,8 @@ int learned_order(gsk_ctx* h, int32_t n_cols, const int32_t* cols, const double*
 int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols,
                const int32_t* cols, const gsk_options* opt, double* G, int32_t* iters,
                int32_t* status, double* resid);
+int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols, const int32_t* cols,
+                  const gsk_options* opt, int32_t* best_w);
 int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
               void* stream);
 }

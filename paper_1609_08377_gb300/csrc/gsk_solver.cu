@@ -211,7 +211,12 @@ __device__ void finalize_all(const RedArgs& r) {
 // ===========================================================================
 // K1: block SpMM  Y[:, lanes] = S X[:, lanes]  (S = A or B, W lanes)
 // ===========================================================================
-enum SpmmMode : int { SP_DOT = 0, SP_RESID = 1 };
+// SP_DOT: Y = S X and the per-lane dot X.Y (own rows).
+// SP_RESID: Y = P = u - S X (refinement residual), Z = 0, dot Y.Y.
+// SP_CG: one CG step with the direction update folded in: X = r (gathered);
+//   for own rows p <- r + b p and Y = B p <- B r + b (B p) with the lane's
+//   direction coefficient b (0 starts a new direction), dot p.(B p).
+enum SpmmMode : int { SP_DOT = 0, SP_RESID = 1, SP_CG = 2 };
 
 template <typename TV, typename TX, typename TY>
 struct SpmmArgs {
@@ -387,18 +392,34 @@ struct DfOps {
   }
 };
 
-// Product of one atom's block row with W lanes of X; acc[a][i] for row a,
-// lane lane0+i. Neighbour rows are fetched 32 at a time with one coalesced
-// load per warp and broadcast by shuffles; two neighbour blocks are processed
-// per iteration so that their loads are in flight together.
-template <class Ops, int L>
-__device__ __forceinline__ void atom_row_product(const Layout& g, const typename Ops::V* __restrict__ val,
-                                                 const typename Ops::X* __restrict__ X, int W, int lane0, int I,
-                                                 typename Ops::Acc (&acc)[4][L], int& oI, int& r0) {
+// Split traversal: each thread owns 4 consecutive lanes (16- or 32-byte X
+// loads); the warp's 32 / (W / 4) = G thread groups each take every G-th
+// neighbour block of the same atom, so a warp runs G independent load chains
+// without divergence; the groups' partial sums are combined by shuffles.
+template <typename T>
+__device__ __forceinline__ void combine_groups(T& v, int G) {
+  for (int m = 32 / G; m < 32; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+}
+__device__ __forceinline__ void combine_groups(dfacc& v, int G) {
+  for (int m = 32 / G; m < 32; m <<= 1) {
+    const float ohi = __shfl_xor_sync(0xffffffffu, v.hi, m);
+    const float olo = __shfl_xor_sync(0xffffffffu, v.lo, m);
+    const df s = two_sum(v.hi, ohi);
+    v.hi = s.hi;
+    v.lo = s.lo + (v.lo + olo);
+  }
+}
+
+template <class Ops, int L, int G>
+__device__ __forceinline__ void atom_row_product_split(const Layout& g, const typename Ops::V* __restrict__ val,
+                                                       const typename Ops::X* __restrict__ X, int W, int I,
+                                                       typename Ops::Acc (&acc)[4][L], int& oI, int& r0) {
   using TV = typename Ops::V;
   using TX = typename Ops::X;
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const int grp = lane / (32 / G);
+  const int lane0 = (lane % (32 / G)) * L;
   oI = g.atom_orb[I];
   r0 = g.atom_roff[I];
   const TV* v = val + g.val_ptr[I];
@@ -411,80 +432,104 @@ __device__ __forceinline__ void atom_row_product(const Layout& g, const typename
     for (int base = e0; base < em; base += 32) {
       const int cnt = min(32, em - base);
       const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
-      int t = 0;
-      for (; t + 2 <= cnt; t += 2) {
-        const int ra = __shfl_sync(kFull, myr, t);
-        const int rb = __shfl_sync(kFull, myr, t + 1);
-        Ops::b44(v, xrow(ra), W, acc);
-        Ops::b44(v + 16, xrow(rb), W, acc);
-        v += 32;
-      }
-      if (t < cnt) {
-        Ops::b44(v, xrow(__shfl_sync(kFull, myr, t)), W, acc);
-        v += 16;
+      const TV* vb = v + (size_t)(base - e0) * 16;
+      for (int t0 = 0; t0 < cnt; t0 += 2 * G) {
+        const int ta = t0 + grp, tb = t0 + G + grp;
+        const int ra = __shfl_sync(kFull, myr, ta & 31);
+        const int rb = __shfl_sync(kFull, myr, tb & 31);
+        if (ta < cnt) Ops::b44(vb + ta * 16, xrow(ra), W, acc);
+        if (tb < cnt) Ops::b44(vb + tb * 16, xrow(rb), W, acc);
       }
     }
+    const TV* vh = v + (size_t)(em - e0) * 16;
     for (int base = em; base < e1; base += 32) {
       const int cnt = min(32, e1 - base);
       const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
-      int t = 0;
-      for (; t + 4 <= cnt; t += 4) {
-        Ops::b41(v, xrow(__shfl_sync(kFull, myr, t)), acc);
-        Ops::b41(v + 4, xrow(__shfl_sync(kFull, myr, t + 1)), acc);
-        Ops::b41(v + 8, xrow(__shfl_sync(kFull, myr, t + 2)), acc);
-        Ops::b41(v + 12, xrow(__shfl_sync(kFull, myr, t + 3)), acc);
-        v += 16;
-      }
-      for (; t < cnt; ++t) {
-        Ops::b41(v, xrow(__shfl_sync(kFull, myr, t)), acc);
-        v += 4;
+      const TV* vb = vh + (size_t)(base - em) * 4;
+      for (int t0 = 0; t0 < cnt; t0 += 4 * G) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int t = t0 + k * G + grp;
+          const int rr = __shfl_sync(kFull, myr, t & 31);
+          if (t < cnt) Ops::b41(vb + t * 4, xrow(rr), acc);
+        }
       }
     }
   } else {
     for (int base = e0; base < em; base += 32) {
       const int cnt = min(32, em - base);
       const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
-      int t = 0;
-      for (; t + 2 <= cnt; t += 2) {
-        const TX* xa = xrow(__shfl_sync(kFull, myr, t));
-        const TX* xb = xrow(__shfl_sync(kFull, myr, t + 1));
-        Ops::b14(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
-        Ops::b14(v + 4, xb, xb + W, xb + 2 * W, xb + 3 * W, acc);
-        v += 8;
-      }
-      if (t < cnt) {
-        const TX* xa = xrow(__shfl_sync(kFull, myr, t));
-        Ops::b14(v, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
-        v += 4;
+      const TV* vb = v + (size_t)(base - e0) * 4;
+      for (int t0 = 0; t0 < cnt; t0 += 2 * G) {
+        const int ta = t0 + grp, tb = t0 + G + grp;
+        const int ra = __shfl_sync(kFull, myr, ta & 31);
+        const int rb = __shfl_sync(kFull, myr, tb & 31);
+        if (ta < cnt) {
+          const TX* xa = xrow(ra);
+          Ops::b14(vb + ta * 4, xa, xa + W, xa + 2 * W, xa + 3 * W, acc);
+        }
+        if (tb < cnt) {
+          const TX* xb = xrow(rb);
+          Ops::b14(vb + tb * 4, xb, xb + W, xb + 2 * W, xb + 3 * W, acc);
+        }
       }
     }
-    // 1-orbital neighbours come padded to a multiple of 4
+    // 1-orbital neighbours come padded to a multiple of 4: one value quad per 4 neighbours
+    const TV* vh = v + (size_t)(em - e0) * 4;
     for (int base = em; base < e1; base += 32) {
       const int cnt = min(32, e1 - base);
       const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
-      for (int t = 0; t < cnt; t += 4) {
-        Ops::b14(v, xrow(__shfl_sync(kFull, myr, t)), xrow(__shfl_sync(kFull, myr, t + 1)),
-                               xrow(__shfl_sync(kFull, myr, t + 2)), xrow(__shfl_sync(kFull, myr, t + 3)), acc);
-        v += 4;
+      const TV* vb = vh + (base - em);
+      const int nq = cnt / 4;
+      for (int q0 = 0; q0 < nq; q0 += G) {
+        const int q = q0 + grp;
+        const int r0q = __shfl_sync(kFull, myr, (4 * q) & 31);
+        const int r1q = __shfl_sync(kFull, myr, (4 * q + 1) & 31);
+        const int r2q = __shfl_sync(kFull, myr, (4 * q + 2) & 31);
+        const int r3q = __shfl_sync(kFull, myr, (4 * q + 3) & 31);
+        if (q < nq) Ops::b14(vb + 4 * q, xrow(r0q), xrow(r1q), xrow(r2q), xrow(r3q), acc);
       }
     }
   }
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < L; ++i) combine_groups(acc[a][i], G);
+  }
 }
 
-template <typename TV, typename TX, typename TY, typename TA, int L, int MODE>
+// Lanes per thread of the SpMM traversal: 4 for FP32 data (16-byte loads),
+// 2 for 8-byte values or lanes (4 when the batch is 128 wide).
+template <typename TV, typename TX, int LW>
+constexpr int spmm_lanes() {
+  return (sizeof(TV) == 4 && sizeof(TX) == 4) ? 4 : (LW > 2 ? LW : 2);
+}
+
+template <typename TV, typename TX, typename TY, typename TA, int LW, int MODE>
 __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a) {
+  // W = 32 * LW lanes; each thread owns L lanes, L / LW thread groups per warp
+  constexpr int L = spmm_lanes<TV, TX, LW>();
+  constexpr int G = L / LW;
   const int W = a.red.W;
-  const int lane0 = (threadIdx.x & 31) * L;
+  const int lane = threadIdx.x & 31;
+  const bool writer = lane < 32 / G;
+  const int lane0 = (lane % (32 / G)) * L;
   const int warp = threadIdx.x >> 5;
   TA dot[L];
+  TY cb[L];
 #pragma unroll
-  for (int i = 0; i < L; ++i) dot[i] = TA(0);
-  const int a0 = blockIdx.x * a.g.chunk;
-  const int a1 = min(a0 + a.g.chunk, a.g.n_atoms);
-  for (int I = a0 + warp; I < a1; I += kWarps) {
+  for (int i = 0; i < L; ++i) {
+    dot[i] = TA(0);
+    cb[i] = (MODE == SP_CG) ? TY(a.red.c.cg_b[lane0 + i]) : TY(0);
+  }
+  const int gw = blockIdx.x * kWarps + warp;
+  const int a1 = a.g.warp_atoms[gw + 1];
+  for (int I = a.g.warp_atoms[gw]; I < a1; ++I) {
     TA acc[4][L];
     int oI, r0;
-    atom_row_product<PlainOps<TV, TX, TA, L>, L>(a.g, a.val, a.X, W, lane0, I, acc, oI, r0);
+    atom_row_product_split<PlainOps<TV, TX, TA, L>, L, G>(a.g, a.val, a.X, W, I, acc, oI, r0);
+    if (!writer) continue;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (r >= oI) break;
@@ -498,6 +543,21 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
         ld_lanes<TX, L>(a.X + base, xo);
 #pragma unroll
         for (int i = 0; i < L; ++i) dot[i] = fmadd<TA>(TA(xo[i]), TA(y[i]), dot[i]);
+      } else if constexpr (MODE == SP_CG) {
+        TX ro[L];
+        TY po[L], so[L];
+        ld_lanes<TX, L>(a.X + base, ro);
+        ld_lanes<TY, L>(a.P + base, po);
+        ld_lanes<TY, L>(a.Y + base, so);
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          const bool fresh = (cb[i] == TY(0));
+          po[i] = fresh ? TY(ro[i]) : fmadd<TY>(cb[i], po[i], TY(ro[i]));
+          y[i] = fresh ? TY(acc[r][i]) : fmadd<TY>(cb[i], so[i], TY(acc[r][i]));
+          dot[i] = fmadd<TA>(TA(po[i]), TA(y[i]), dot[i]);
+        }
+        st_lanes<TY, L>(a.P + base, po);
+        st_lanes<TY, L>(a.Y + base, y);
       } else {
         double uu[L];
         ld_lanes<double, L>(a.U + base, uu);
@@ -517,7 +577,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
   double d[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) d[i] = double(dot[i]);
-  lane_reduce_commit<L>(d, a.red);
+  lane_reduce_commit_at<L>(d, a.red, lane0, writer);
 }
 
 // Double-float SpMM: Y = S X (SP_DOT: X = q in double-float, Y double-float,
@@ -536,10 +596,14 @@ struct SpmmDfArgs {
   RedArgs red;
 };
 
-template <typename TX, int L, int MODE>
+template <typename TX, int LW, int MODE>
 __global__ void __launch_bounds__(kThreads) k_spmm_df(const SpmmDfArgs<TX> a) {
+  constexpr int L = spmm_lanes<float2, TX, LW>();
+  constexpr int G = L / LW;
   const int W = a.red.W;
-  const int lane0 = (threadIdx.x & 31) * L;
+  const int lane = threadIdx.x & 31;
+  const bool writer = lane < 32 / G;
+  const int lane0 = (lane % (32 / G)) * L;
   const int warp = threadIdx.x >> 5;
   dfacc dacc[L];
   float facc[L];
@@ -548,12 +612,13 @@ __global__ void __launch_bounds__(kThreads) k_spmm_df(const SpmmDfArgs<TX> a) {
     acc_zero(dacc[i]);
     facc[i] = 0.f;
   }
-  const int a0 = blockIdx.x * a.g.chunk;
-  const int a1 = min(a0 + a.g.chunk, a.g.n_atoms);
-  for (int I = a0 + warp; I < a1; I += kWarps) {
+  const int gw = blockIdx.x * kWarps + warp;
+  const int a1 = a.g.warp_atoms[gw + 1];
+  for (int I = a.g.warp_atoms[gw]; I < a1; ++I) {
     dfacc acc[4][L];
     int oI, r0;
-    atom_row_product<DfOps<TX, L>, L>(a.g, a.val, a.X, W, lane0, I, acc, oI, r0);
+    atom_row_product_split<DfOps<TX, L>, L, G>(a.g, a.val, a.X, W, I, acc, oI, r0);
+    if (!writer) continue;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (r >= oI) break;
@@ -589,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_df(const SpmmDfArgs<TX> a) {
   double d[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) d[i] = (MODE == SP_DOT) ? df_to_double(acc_value(dacc[i])) : (double)facc[i];
-  lane_reduce_commit<L>(d, a.red);
+  lane_reduce_commit_at<L>(d, a.red, lane0, writer);
 }
 
 // ===========================================================================
@@ -703,27 +768,6 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(const VecArgs a) {
 #pragma unroll
   for (int i = 0; i < L; ++i) d[i] = double(acc[i]);
   lane_reduce_commit<L>(d, a.red);
-}
-
-// K_P: p = r + b p
-template <typename T, int L>
-__global__ void __launch_bounds__(kThreads) k_cg_dir(const VecArgs a) {
-  const int W = a.red.W;
-  const int lane0 = (threadIdx.x & 31) * L;
-  T cb[L];
-#pragma unroll
-  for (int i = 0; i < L; ++i) cb[i] = T(a.red.c.cg_b[lane0 + i]);
-  const T* r = static_cast<const T*>(a.r);
-  T* p = static_cast<T*>(a.p);
-  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
-    const size_t base = (size_t)row * W + lane0;
-    T pv[L], rv[L];
-    ld_lanes<T, L>(p + base, pv);
-    ld_lanes<T, L>(r + base, rv);
-#pragma unroll
-    for (int i = 0; i < L; ++i) pv[i] = fmadd<T>(cb[i], pv[i], rv[i]);
-    st_lanes<T, L>(p + base, pv);
-  }
 }
 
 // v = x (FP64 mode) or v0 + d (mixed mode)
@@ -1245,7 +1289,7 @@ struct Plan {
   SpmmArgs<double, float, float> spR;
   SpmmDfArgs<float2> spAdf;
   SpmmDfArgs<float> spRdf;
-  VecArgs upd, cgu[2], cgp[2], dot, fin;
+  VecArgs upd, cgu[2], dot, fin;
   ShiftArgs sh;
   PrimeArgs prime;
   WrapArgs wrap;
@@ -1255,17 +1299,17 @@ template <int L>
 struct Kernels {
   // FP64 mode
   static constexpr auto spmm64 = k_spmm<double, double, double, double, L, SP_DOT>;
+  static constexpr auto spmm64cg = k_spmm<double, double, double, double, L, SP_CG>;
   static constexpr auto upd64 = k_update<double, L>;
   static constexpr auto cgu64 = k_cg_update<double, L>;
-  static constexpr auto cgp64 = k_cg_dir<double, L>;
   static constexpr auto dot64 = k_dot_uv<double, L, false>;
   static constexpr auto fin64 = k_finish<double, L, false>;
   // mixed mode
   static constexpr auto spmm32 = k_spmm<float, float, float, float, L, SP_DOT>;
+  static constexpr auto spmm32cg = k_spmm<float, float, float, float, L, SP_CG>;
   static constexpr auto resid = k_spmm<double, float, float, double, L, SP_RESID>;
   static constexpr auto upd32 = k_update<float, L>;
   static constexpr auto cgu32 = k_cg_update<float, L>;
-  static constexpr auto cgp32 = k_cg_dir<float, L>;
   static constexpr auto dotm = k_dot_uv<float, L, true>;
   static constexpr auto finm = k_finish<float, L, true>;
   // mixed mode, double-float refinement
@@ -1306,13 +1350,11 @@ cudaError_t launch_cg_iteration(const Plan& P, Launcher& la, int pass) {
   using K = Kernels<L>;
   const dim3 blk(kThreads);
   if (!P.mixed) {
-    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spB64, spmm_smem<double, double, L>()));
+    GSK_CUDA_TRY(la(K::spmm64cg, dim3(P.grid_rows), blk, P.spB64));
     GSK_CUDA_TRY(la(K::cgu64, dim3(P.grid_vec), blk, P.cgu[0]));
-    GSK_CUDA_TRY(la(K::cgp64, dim3(P.grid_vec), blk, P.cgp[0]));
   } else {
-    GSK_CUDA_TRY(la(K::spmm32, dim3(P.grid_rows), blk, P.spB32[pass], spmm_smem<float, float, L>()));
+    GSK_CUDA_TRY(la(K::spmm32cg, dim3(P.grid_rows), blk, P.spB32[pass]));
     GSK_CUDA_TRY(la(K::cgu32, dim3(P.grid_vec), blk, P.cgu[pass]));
-    GSK_CUDA_TRY(la(K::cgp32, dim3(P.grid_vec), blk, P.cgp[pass]));
   }
   return cudaSuccess;
 }
@@ -1405,7 +1447,7 @@ cudaError_t build_graph(Plan& P, cudaGraphExec_t* exec) {
     // propagate graph control into every argument block
     RedArgs* reds[] = {&P.spA.red, &P.spB64.red, &P.spB32[0].red, &P.spB32[1].red, &P.spR.red,
                        &P.spAdf.red, &P.spRdf.red,
-                       &P.upd.red, &P.cgu[0].red, &P.cgu[1].red, &P.cgp[0].red, &P.cgp[1].red,
+                       &P.upd.red, &P.cgu[0].red, &P.cgu[1].red,
                        &P.dot.red, &P.fin.red};
     for (RedArgs* r : reds) r->gc = gc;
     GraphBuilder gb(body);
@@ -1517,6 +1559,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   P.df = (opt.precision == GSK_MIXED_DF);
   P.refine = P.mixed && opt.refine != 0;
   int W = opt.batch_w;
+  if (W == 0 && h->tuned_w[opt.precision] != 0) W = h->tuned_w[opt.precision];
   if (W == 0) {
     // lanes in flight: enough columns to fill the batch, favouring wide batches
     W = (n_cols > 64 && P.mixed) ? 128 : 64;
@@ -1683,9 +1726,11 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
 
   const Layout& g = h->lay;
   P.spA = {g, h->d_A64.as<double>(), q, u, nullptr, nullptr, nullptr, red(FIN_ALPHA)};
-  P.spB64 = {g, h->d_B64.as<double>(), static_cast<double*>(p), static_cast<double*>(Bp), nullptr, nullptr, nullptr, red(FIN_CG_A)};
+  P.spB64 = {g, h->d_B64.as<double>(), static_cast<double*>(r), static_cast<double*>(Bp), nullptr,
+             static_cast<double*>(p), nullptr, red(FIN_CG_A)};
   for (int ps = 0; ps < 2; ++ps)
-    P.spB32[ps] = {g, h->d_B32.as<float>(), static_cast<float*>(p), static_cast<float*>(Bp), nullptr, nullptr, nullptr, red(FIN_CG_A)};
+    P.spB32[ps] = {g, h->d_B32.as<float>(), static_cast<float*>(r), static_cast<float*>(Bp), nullptr,
+                   static_cast<float*>(p), nullptr, red(FIN_CG_A)};
   P.spR = {g, h->d_B64.as<double>(), static_cast<float*>(x), static_cast<float*>(r), u, static_cast<float*>(p), static_cast<float*>(x2), red(FIN_RESID)};
   P.spAdf = {g, h->d_A2.as<float2>(), reinterpret_cast<const float2*>(q), reinterpret_cast<float2*>(u), nullptr,
              nullptr, nullptr, nullptr, red(FIN_ALPHA)};
@@ -1700,8 +1745,6 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
     P.cgu[ps].x = ps == 0 ? x : x2;
     P.cgu[ps].red = red(FIN_CG_RR);
     P.cgu[ps].red.max_iter = ps == 0 ? opt.max_iter : -1;
-    P.cgp[ps] = va;
-    P.cgp[ps].red = red(FIN_SUM);
   }
   P.dot = va; P.dot.red = red(FIN_BETA);
   P.fin = va; P.fin.red = red(FIN_SUM);
@@ -1759,7 +1802,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
     h->last.outer_steps = steps;
     h->last.cg_iterations = cgt;
     const int64_t per_step = 3 + 2 + ((P.mixed && P.refine) ? 1 : 0);
-    h->last.kernel_launches = 3 + steps * per_step + cgt * 3;
+    h->last.kernel_launches = 3 + steps * per_step + cgt * 2;
     h->last.batch_w = W;
     h->last.used_graph = opt.use_graph ? 1 : 0;
   }
@@ -1832,6 +1875,69 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
     }
     if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
   }
+  return GSK_OK;
+}
+
+}  // namespace gsk
+
+namespace gsk {
+
+int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_t n_cols, const int32_t* cols,
+                  const gsk_options* opt_in, int32_t* best_w) {
+  if (!best_w || n_cols < 1 || !cols) return GSK_EINVAL;
+  gsk_options opt;
+  gsk_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.precision < GSK_FP64 || opt.precision > GSK_MIXED_DF) return GSK_EINVAL;
+  if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(opt.stream);
+  const int cands[3] = {32, 64, 128};
+  const int n_cand = (opt.precision == GSK_FP64) ? 2 : 3;
+  double best = 1e300;
+  int pick = 64;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GSK_ECUDA;
+  int rc = GSK_OK;
+  for (int ci = 0; ci < n_cand && rc == GSK_OK; ++ci) {
+    const int W = cands[ci];
+    const int n = std::min(n_cols, W);
+    // device buffer for the truncated solve's G
+    int64_t elems = 0;
+    for (int c = 0; c < n; ++c) elems += h->row_ptr[cols[c] + 1] - h->row_ptr[cols[c]];
+    if (h->ws_tune.ensure((size_t)elems * S * 16 + 256) != cudaSuccess) {
+      rc = GSK_ENOMEM;
+      break;
+    }
+    gsk_options o = opt;
+    o.batch_w = W;
+    o.max_iter = 24;
+    o.tol = 1e-30;
+    o.sched = GSK_SCHED_FIFO;
+    double ms_per_step = 0.0;
+    for (int rep = 0; rep < 2 && rc == GSK_OK; ++rep) {     // first run warms up and builds nothing persistent
+      cudaEventRecord(e0, s);
+      rc = solve_impl(h, S, z, eta, n, cols, &o, h->ws_tune.as<double>(), nullptr, nullptr, nullptr);
+      cudaEventRecord(e1, s);
+      if (rc != GSK_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = GSK_ECUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_per_step = ms / std::max<int64_t>(1, h->last.outer_steps);
+    }
+    const double est = ms_per_step * std::max((double)n_cols / W, 2.0);
+    if (rc == GSK_OK && est < best) {
+      best = est;
+      pick = W;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GSK_OK) return rc;
+  h->tuned_w[opt.precision] = pick;
+  *best_w = pick;
   return GSK_OK;
 }
 

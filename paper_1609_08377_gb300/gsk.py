@@ -72,6 +72,7 @@ def _load() -> C.CDLL:
         "gsk_mlp_workspace_bytes": (C.c_size_t, [I32]),
         "gsk_mlp_train_step": (C.c_int, [I32, P, P, P, P, P, P, I32, C.c_float, P, P, P, P]),
         "gsk_set_sched_model": (C.c_int, [P, P, P]),
+        "gsk_autotune": (C.c_int, [P, I32, P, P, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -216,6 +217,18 @@ class Solver:
                             _ptr(iters), _ptr(status), _ptr(resid))
         _check(rc, "gsk_solve")
         return iters, status, resid
+
+    def autotune(self, z, cols, eta=None, **kw) -> int:
+        """gsk_autotune: pick and cache the lane width for this precision."""
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+        zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).ravel())
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        opt = default_options(**kw)
+        w = C.c_int32()
+        _check(_lib.gsk_autotune(self._h, z.size, _ptr(zz), _ptr(e), cols.size, _ptr(cols), C.byref(opt),
+                                 C.byref(w)), "gsk_autotune")
+        return int(w.value)
 
     def density(self, G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=None) -> None:
         eps = np.ascontiguousarray(eps, dtype=np.float64)
