@@ -349,17 +349,24 @@ def spmm_roofline(solver, sys_, args, stream, dev) -> dict:
     bv = 4 if prec == gsk.GSK_MIXED else 8
     nnz = sys_.nnz
     n_atoms = sys_.n_atoms
-    # algorithmic bytes: stored values once, neighbour index per atom block,
-    # block-row pointers, X read once, Y written once
+    # algorithmic bytes of the inner CG's product: stored values once, neighbour
+    # index per atom block, block-row pointers, r read once, direction p and
+    # B p each read and written once
     n_blocks = _atom_blocks(sys_)
-    alg = nnz * bv + n_blocks * 4 + (n_atoms + 1) * 4 + 2 * M * W * bv
+    alg = nnz * bv + n_blocks * 4 + (n_atoms + 1) * 4 + 5 * M * W * bv
     peaks = _peaks()
     achieved = alg / sec / 1e9
+    # DRAM bytes (read + write) per launch of this kernel from one ncu capture
+    # (summarised in profiles/spmm_cg_fp32_ch20k_w64.md); None for other shapes
+    traffic = _NCU_TRAFFIC.get((args.workload, bv, W))
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "kernel": f"k_spmm (B, {'FP32' if bv == 4 else 'FP64'}, W={W}) x{reps} via gsk_spmm",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": f"k_spmm (inner-CG B product, {'FP32' if bv == 4 else 'FP64'}, W={W}) x{reps} via gsk_spmm",
             "ms_per_launch": sec * 1e3, "alg_bytes_per_launch": int(alg),
             "peak_source": peaks["source"]}
+
+
+_NCU_TRAFFIC = {("ch20k", 4, 64): 53.08e6}
 
 
 def _atom_blocks(sys_) -> int:

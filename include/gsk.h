@@ -94,7 +94,7 @@ typedef struct {
   int32_t batch_w;      /* lanes (columns in flight): 32, 64 or 128; 0 = autotune (default) */
   int32_t refine;       /* GSK_MIXED only: 1 = FP64 residual correction of each B-solve (default), 0 = none */
   int32_t sched;        /* GSK_SCHED_FIFO (default) or GSK_SCHED_LEARNED (model set with gsk_set_sched_model) */
-  double inner_tol;     /* relative residual of each B-solve; 0 = default (1e-12 FP64, 1e-6 per FP32 pass) */
+  double inner_tol;     /* relative residual of each B-solve; 0 = default (1e-12 FP64, 3e-6 per FP32 pass) */
   int32_t max_inner;    /* CG iteration cap per B-solve pass; default 200 */
   int32_t use_graph;    /* 1 = run the solve as one captured CUDA graph with device-side loops (default) */
   void* stream;         /* cudaStream_t to run on; NULL = the legacy default stream */
@@ -197,9 +197,10 @@ int gsk_row_order(gsk_handle h, int32_t* row_lib);
 
 /* n_rep applications of the solver's block SpMM kernel, Y = S X with S = A
  * (which = 0) or B (which = 1), on W lanes (32, 64 or 128; 128 only for
- * FP32): the same kernel, launch shape and epilogue (per-lane dot X.Y, kept
- * internally) that gsk_solve runs, for timing and for callers working in the
- * library's row order.
+ * FP32): the same kernel, launch shape and epilogue that gsk_solve runs, for
+ * timing and for callers working in the library's row order. For B it is the
+ * inner CG's kernel, which also sets a direction vector P = X (internal) and
+ * forms the per-lane dot P.Y; for A it forms the dot X.Y.
  *   precision GSK_FP64: X, Y are double; GSK_MIXED: X, Y are float
  *   X, Y      device, M x W row-major (lane fastest), rows in library order
  *   stream    cudaStream_t or NULL. Asynchronous on that stream. */

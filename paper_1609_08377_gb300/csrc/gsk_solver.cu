@@ -733,11 +733,17 @@ __global__ void __launch_bounds__(kThreads) k_update(const VecArgs a) {
   lane_reduce_commit<L>(d, a.red);
 }
 
-// K_C: x += a p, r -= a Bp, r.r
-template <typename T, int L>
+// K_C: x += a p, r -= a Bp, r.r. Each thread owns 4 consecutive lanes
+// (16-byte loads for FP32); a warp covers 128 / W rows per pass, and the
+// per-lane sums of the rows a warp covers are combined by shuffles.
+template <typename T, int LW>
 __global__ void __launch_bounds__(kThreads) k_cg_update(const VecArgs a) {
+  constexpr int L = 4;
+  constexpr int RPW = 4 / LW;            // rows per warp pass (W = 32 * LW)
   const int W = a.red.W;
-  const int lane0 = (threadIdx.x & 31) * L;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / (32 / RPW);     // which of the warp's rows
+  const int lane0 = (lane % (32 / RPW)) * L;
   T ca[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) ca[i] = T(a.red.c.cg_a[lane0 + i]);
@@ -748,26 +754,32 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(const VecArgs a) {
   T acc[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) acc[i] = T(0);
-  for (int row = vec_warp_id(); row < a.M; row += vec_warp_count()) {
-    const size_t base = (size_t)row * W + lane0;
-    T pv[L], bv[L], xv[L], rv[L];
-    ld_lanes<T, L>(p + base, pv);
-    ld_lanes<T, L>(Bp + base, bv);
-    ld_lanes<T, L>(x + base, xv);
-    ld_lanes<T, L>(r + base, rv);
+  for (int row0 = vec_warp_id() * RPW; row0 < a.M; row0 += vec_warp_count() * RPW) {
+    const int row = row0 + sub;
+    if (row < a.M) {
+      const size_t base = (size_t)row * W + lane0;
+      T pv[L], bv[L], xv[L], rv[L];
+      ld_lanes<T, L>(p + base, pv);
+      ld_lanes<T, L>(Bp + base, bv);
+      ld_lanes<T, L>(x + base, xv);
+      ld_lanes<T, L>(r + base, rv);
 #pragma unroll
-    for (int i = 0; i < L; ++i) {
-      xv[i] = fmadd<T>(ca[i], pv[i], xv[i]);
-      rv[i] = fmadd<T>(-ca[i], bv[i], rv[i]);
-      acc[i] = fmadd<T>(rv[i], rv[i], acc[i]);
+      for (int i = 0; i < L; ++i) {
+        xv[i] = fmadd<T>(ca[i], pv[i], xv[i]);
+        rv[i] = fmadd<T>(-ca[i], bv[i], rv[i]);
+        acc[i] = fmadd<T>(rv[i], rv[i], acc[i]);
+      }
+      st_lanes<T, L>(x + base, xv);
+      st_lanes<T, L>(r + base, rv);
     }
-    st_lanes<T, L>(x + base, xv);
-    st_lanes<T, L>(r + base, rv);
   }
   double d[L];
 #pragma unroll
-  for (int i = 0; i < L; ++i) d[i] = double(acc[i]);
-  lane_reduce_commit<L>(d, a.red);
+  for (int i = 0; i < L; ++i) {
+    d[i] = double(acc[i]);
+    for (int m = 32 / RPW; m < 32; m <<= 1) d[i] += __shfl_xor_sync(0xffffffffu, d[i], m);
+  }
+  lane_reduce_commit_at<L>(d, a.red, lane0, sub == 0);
 }
 
 // v = x (FP64 mode) or v0 + d (mixed mode)
@@ -1714,7 +1726,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   gc.max_inner = opt.max_inner;
   const int per_lane = (n_cols + W - 1) / W + 1;
   gc.step_cap = (int)std::min<int64_t>((int64_t)(opt.max_iter + 2) * per_lane, 2000000000LL);
-  const double itol = (opt.inner_tol > 0.0) ? opt.inner_tol : (P.mixed ? 1e-6 : 1e-12);
+  const double itol = (opt.inner_tol > 0.0) ? opt.inner_tol : (P.mixed ? 3e-6 : 1e-12);
   RedArgs rb{};
   rb.c = c;
   rb.jobs = jobs;
@@ -1833,12 +1845,16 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
                             (size_t)n_grp_max * kMaxW * sizeof(double) + n_grp_max * sizeof(unsigned) + 256;
   if (grid > kMaxRedCtas) return GSK_ENOTSUP;
   if (h->ws_lane.ensure(lane_bytes) != cudaSuccess) return GSK_ENOMEM;
+  // direction vector of the CG form of the product (B): M x W, zero coefficient
+  const size_t esz = precision == GSK_FP64 ? sizeof(double) : sizeof(float);
+  if (which == 1 && h->ws_misc.ensure((size_t)h->M * W * esz + 256) != cudaSuccess) return GSK_ENOMEM;
   char* lb = h->ws_lane.as<char>();
   if (cudaMemsetAsync(lb, 0, lane_bytes, s) != cudaSuccess) return GSK_ECUDA;
   LaneCtl c{};
   c.red_out = reinterpret_cast<double*>(lb);
-  c.red_counter = reinterpret_cast<unsigned int*>(lb + kMaxW * sizeof(double));
-  c.partials = reinterpret_cast<double*>(lb + 2 * kMaxW * sizeof(double));
+  c.cg_b = reinterpret_cast<double*>(lb + kMaxW * sizeof(double));             // all zero
+  c.red_counter = reinterpret_cast<unsigned int*>(lb + 2 * kMaxW * sizeof(double));
+  c.partials = reinterpret_cast<double*>(lb + 3 * kMaxW * sizeof(double));
   c.grp_partials = c.partials + (size_t)grid * kMaxW;
   c.grp_counter = reinterpret_cast<unsigned int*>(c.grp_partials + (size_t)n_grp_max * kMaxW);
   RedArgs r{};
@@ -1846,31 +1862,31 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
   r.fin = FIN_SUM;
   r.W = W;
   const dim3 blk(kThreads), grd(grid);
+  void* P = which == 1 ? h->ws_misc.ptr : nullptr;
   for (int i = 0; i < n_rep; ++i) {
     if (precision == GSK_FP64) {
       SpmmArgs<double, double, double> a{h->lay, (which ? h->d_B64 : h->d_A64).as<double>(),
                                          static_cast<const double*>(X), static_cast<double*>(Y),
-                                         nullptr, nullptr, nullptr, r};
-      if (W == 32) {
-        allow_smem(k_spmm<double, double, double, double, 1, SP_DOT>, spmm_smem<double, double, 1>());
-        k_spmm<double, double, double, double, 1, SP_DOT><<<grd, blk, spmm_smem<double, double, 1>(), s>>>(a);
+                                         nullptr, static_cast<double*>(P), nullptr, r};
+      if (which == 1) {
+        if (W == 32) k_spmm<double, double, double, double, 1, SP_CG><<<grd, blk, 0, s>>>(a);
+        else k_spmm<double, double, double, double, 2, SP_CG><<<grd, blk, 0, s>>>(a);
       } else {
-        allow_smem(k_spmm<double, double, double, double, 2, SP_DOT>, spmm_smem<double, double, 2>());
-        k_spmm<double, double, double, double, 2, SP_DOT><<<grd, blk, spmm_smem<double, double, 2>(), s>>>(a);
+        if (W == 32) k_spmm<double, double, double, double, 1, SP_DOT><<<grd, blk, 0, s>>>(a);
+        else k_spmm<double, double, double, double, 2, SP_DOT><<<grd, blk, 0, s>>>(a);
       }
     } else {
       SpmmArgs<float, float, float> a{h->lay, (which ? h->d_B32 : h->d_A32).as<float>(),
                                       static_cast<const float*>(X), static_cast<float*>(Y),
-                                      nullptr, nullptr, nullptr, r};
-      if (W == 32) {
-        allow_smem(k_spmm<float, float, float, float, 1, SP_DOT>, spmm_smem<float, float, 1>());
-        k_spmm<float, float, float, float, 1, SP_DOT><<<grd, blk, spmm_smem<float, float, 1>(), s>>>(a);
-      } else if (W == 64) {
-        allow_smem(k_spmm<float, float, float, float, 2, SP_DOT>, spmm_smem<float, float, 2>());
-        k_spmm<float, float, float, float, 2, SP_DOT><<<grd, blk, spmm_smem<float, float, 2>(), s>>>(a);
+                                      nullptr, static_cast<float*>(P), nullptr, r};
+      if (which == 1) {
+        if (W == 32) k_spmm<float, float, float, float, 1, SP_CG><<<grd, blk, 0, s>>>(a);
+        else if (W == 64) k_spmm<float, float, float, float, 2, SP_CG><<<grd, blk, 0, s>>>(a);
+        else k_spmm<float, float, float, float, 4, SP_CG><<<grd, blk, 0, s>>>(a);
       } else {
-        allow_smem(k_spmm<float, float, float, float, 4, SP_DOT>, spmm_smem<float, float, 4>());
-        k_spmm<float, float, float, float, 4, SP_DOT><<<grd, blk, spmm_smem<float, float, 4>(), s>>>(a);
+        if (W == 32) k_spmm<float, float, float, float, 1, SP_DOT><<<grd, blk, 0, s>>>(a);
+        else if (W == 64) k_spmm<float, float, float, float, 2, SP_DOT><<<grd, blk, 0, s>>>(a);
+        else k_spmm<float, float, float, float, 4, SP_DOT><<<grd, blk, 0, s>>>(a);
       }
     }
     if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
