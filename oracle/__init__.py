@@ -14,7 +14,13 @@ Modules:
              shift (Sec. III-B, shared Krylov subspace for all shifts);
              O3': plain COCG on z B - A, one shift at a time.
   density -- Fermi function (Eq. EQ-FD-FUNC) and the density matrix on the
-             pattern by quadrature of Eq. EQ-DM-GREEN-FN.
+             pattern by quadrature of Eq. EQ-DM-GREEN-FN; per-shift traces,
+             the chemical potential for an electron count (bisection) and
+             the ICOHP connectivity C_IJ (Sec. VII).
+  marnoldi-- the multiple Arnoldi projection of one column (Sec. III-B,
+             Eq. EQ-LS-MULTIPLE): Ritz pairs of the pencil on
+             K(A; e_j) + K(A; B^-1 e_j), G^(j) and rho^(j) by the analytic
+             energy integral.
   mlp     -- the iteration-count regressor used by the column scheduler
              (forward, backward and Adam), in FP64.
   features-- per-column scheduler features.

@@ -339,3 +339,121 @@ def test_sum_rule_fine_grid():
         bound += tail + smooth + 1e-9
     assert abs(trB - want) <= bound
     assert bound < 0.5
+
+
+# ---------------------------------------------------------------------------
+# trace quantities: per-shift traces, chemical potential, ICOHP
+# ---------------------------------------------------------------------------
+
+def test_shift_traces_closed_form(c64):
+    """Full column set: sum_j (G(z)B)_jj = sum_m 1/(z - lambda_m) and
+    sum_j (G(z)A)_jj = sum_m lambda_m/(z - lambda_m) (Eq. EQ-EIG-GREEN)."""
+    eps = syn.energy_grid(16)
+    z = syn.shifts(eps, 0.1)
+    cols = np.arange(c64.M)
+    G = dense.green_lu(c64.A, c64.B, z, cols)
+    off = dense.pattern_offsets(c64.A, cols)
+    lam, _ = dense.generalized_eigh(c64.A, c64.B)
+    r = 1.0 / (z[None, :] - lam[:, None])
+    sB = density.shift_traces(G, c64.B, cols, off)
+    sA = density.shift_traces(G, c64.A, cols, off)
+    assert np.allclose(sB, r.sum(axis=0).imag, rtol=1e-10, atol=1e-10)
+    assert np.allclose(sA, (lam[:, None] * r).sum(axis=0).imag, rtol=1e-10, atol=1e-10)
+    # the count at any mu is the trace of the quadrature density matrix
+    w = syn.trapezoid_weights(eps)
+    rho = density.density_from_green(G, eps, w, -8.0, 0.3)
+    assert np.isclose(density.count_from_traces(sB, eps, w, -8.0, 0.3),
+                      density.trace_with(rho, c64.B, cols, off), rtol=1e-12)
+
+
+def _diag_pencil_green(a, z):
+    """G for A = diag(a), B = I on a diagonal pattern: G_ii = 1/(z - a_i)."""
+    M = a.size
+    A = sp.csr_matrix(np.diag(a))
+    B = sp.identity(M, format="csr")
+    G = 1.0 / (z[None, :] - a[:, None])
+    return A, B, G
+
+
+def test_find_mu_symmetric_spectrum():
+    """Spectrum and grid symmetric about 0, n_elec = half the f = 1 count:
+    f(e) + f(-e) = 1 at mu = 0 makes N(0) exactly that half, so mu = 0."""
+    a = np.array([-3.0, -1.2, -0.4, 0.4, 1.2, 3.0])
+    eps = np.linspace(-6, 6, 241)
+    w = syn.trapezoid_weights(eps)
+    z = syn.shifts(eps, 0.2)
+    A, B, G = _diag_pencil_green(a, z)
+    cols = np.arange(a.size)
+    s = density.shift_traces(G, B, cols, dense.pattern_offsets(A, cols))
+    full = float(-(w @ s) / np.pi)
+    mu = density.find_mu(s, eps, w, 0.1, 0.5 * full, -5.0, 5.0)
+    assert abs(mu) < 1e-12
+
+
+def test_find_mu_gap_and_count():
+    """A gapped spectrum, a fine grid, small eta and kT: the mu that holds three
+    electrons lies inside the gap between the third and fourth level, and the
+    count there matches the target."""
+    a = np.array([-7.0, -6.5, -5.0, -1.0, 0.5, 2.0])
+    eps = np.linspace(-40, 40, 16001)
+    w = syn.trapezoid_weights(eps)
+    z = syn.shifts(eps, 0.02)
+    A, B, G = _diag_pencil_green(a, z)
+    cols = np.arange(a.size)
+    s = density.shift_traces(G, B, cols, dense.pattern_offsets(A, cols))
+    mu = density.find_mu(s, eps, w, 0.05, 3.0, -20.0, 20.0)
+    assert -5.0 < mu < -1.0
+    assert abs(density.count_from_traces(s, eps, w, mu, 0.05) - 3.0) < 1e-10
+    with pytest.raises(ValueError):
+        density.find_mu(s, eps, w, 0.05, 7.0, -20.0, 20.0)
+
+
+def test_icohp_bruteforce_and_energy(c64):
+    """C_IJ against dense blocks of the exact density matrix, the sum rule
+    sum_IJ C_IJ = Tr(rho A) (Sec. VII), and C_IJ = C_JI for a symmetric rho."""
+    eps = syn.energy_grid(16)
+    w = syn.trapezoid_weights(eps)
+    z = syn.shifts(eps, 0.1)
+    mu, kT = -10.0, 0.1
+    cols = np.arange(c64.M)
+    G = dense.green_lu(c64.A, c64.B, z, cols)
+    off = dense.pattern_offsets(c64.A, cols)
+    rho = density.density_from_green(G, eps, w, mu, kT)
+    aptr, aidx, C = density.icohp(rho, c64.A, cols, off, c64.orb_offset, c64.orb_count)
+    # dense rho from the same quadrature, column by column through G = (zB - A)^-1
+    Ad = c64.A.toarray()
+    Rd = np.zeros_like(Ad)
+    coef = w * density.fermi(eps, mu, kT)
+    for k in range(eps.size):
+        Rd += -(coef[k] / np.pi) * dense.green_dense_full(c64.A, c64.B, z[k]).imag
+    oo, oc = c64.orb_offset.astype(int), c64.orb_count.astype(int)
+    for J in range(c64.n_atoms):
+        sJ = slice(oo[J], oo[J] + oc[J])
+        for s in range(aptr[J], aptr[J + 1]):
+            I = int(aidx[s])
+            sI = slice(oo[I], oo[I] + oc[I])
+            want = float((Rd[sI, sJ] * Ad[sJ, sI].T).sum())
+            assert abs(C[s] - want) <= 1e-10 * max(1.0, abs(want))
+    assert np.isclose(C.sum(), density.trace_with(rho, c64.A, cols, off), rtol=1e-12)
+    pos = {(int(aidx[s]), J): s for J in range(c64.n_atoms) for s in range(aptr[J], aptr[J + 1])}
+    for (I, J), s in pos.items():
+        assert abs(C[s] - C[pos[(J, I)]]) <= 1e-10 * max(1.0, abs(C[s]))
+
+
+def test_icohp_column_subset_on_ch_mix():
+    """Mixed C/H atoms and a column subset: only the atoms of solved columns get
+    entries, and the total is Tr(rho A) over those columns."""
+    s_ = syn.make_system(40, 0.5, 3)
+    eps = syn.energy_grid(8)
+    w = syn.trapezoid_weights(eps)
+    z = syn.shifts(eps, 0.2)
+    cols = syn.column_subset(s_.M, 11, 1)
+    G = dense.green_lu(s_.A, s_.B, z, cols)
+    off = dense.pattern_offsets(s_.A, cols)
+    rho = density.density_from_green(G, eps, w, -10.0, 0.1)
+    aptr, aidx, C = density.icohp(rho, s_.A, cols, off, s_.orb_offset, s_.orb_count)
+    atoms = set(s_.atom_of_row()[cols].tolist())
+    for J in range(s_.n_atoms):
+        if J not in atoms:
+            assert not C[aptr[J]:aptr[J + 1]].any()
+    assert np.isclose(C.sum(), density.trace_with(rho, s_.A, cols, off), rtol=1e-12)
