@@ -30,6 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1609_08377_gb300.profile_spmm import atom_blocks, spmm_alg_bytes  # noqa: E402
+
 METRIC = "column·shift solves/s at 1e-8 resid"
 UNIT = "column-shift solves/s"
 
@@ -300,6 +302,27 @@ def main():
     # ---- roofline of the dominant kernel: the block SpMM ----
     roof = spmm_roofline(solver, sys_, args, stream, dev)
 
+    # ---- against the plain FP64 solver: time per lock-step Lanczos step on the
+    # same columns and lane width (both precisions converge in the same number
+    # of steps to within a few per cent, so the per-step ratio is the speed-up)
+    vs_fp64 = None
+    if args.precision != "fp64":
+        c_cmp, e_cmp = batches[args.warmup]
+        per = {}
+        for prec in (args.precision, "fp64"):
+            for rep in range(2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                solver.solve(z, c_cmp, G, eta=e_cmp, precision=prec, tol=1e-8, max_iter=60,
+                             batch_w=tuned_w, sched="fifo", stream=stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+            per[prec] = e0.elapsed_time(e1) / solver.last_stats()["outer_steps"]
+        vs_fp64 = {"ratio": per["fp64"] / per[args.precision], "ms_per_step": per,
+                   "how": f"60 lock-step Lanczos steps of the same {c_cmp.size} columns at W={tuned_w}, "
+                          "CUDA events; iteration counts of the two precisions agree to a few per cent"}
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
@@ -309,6 +332,7 @@ def main():
         "config": workload_config(wl, sys_, S, C, args, world),
         "batch_w": int(solver.last_stats()["batch_w"]), "batch_w_autotuned": args.batch_w == 0,
         "roofline": roof,
+        "vs_plain_fp64": vs_fp64,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clock,
@@ -347,17 +371,10 @@ def spmm_roofline(solver, sys_, args, stream, dev) -> dict:
     torch.cuda.synchronize(dev)
     sec = e0.elapsed_time(e1) / 1e3 / reps
     bv = 4 if prec == gsk.GSK_MIXED else 8
-    nnz = sys_.nnz
-    n_atoms = sys_.n_atoms
-    # algorithmic bytes of the inner CG's product: stored values once, neighbour
-    # index per atom block, block-row pointers, r read once, direction p and
-    # B p each read and written once
-    n_blocks = _atom_blocks(sys_)
-    alg = nnz * bv + n_blocks * 4 + (n_atoms + 1) * 4 + 5 * M * W * bv
+    alg = spmm_alg_bytes(sys_, atom_blocks(sys_), W, bv)
     peaks = _peaks()
     achieved = alg / sec / 1e9
-    # DRAM bytes (read + write) per launch of this kernel from one ncu capture
-    # (summarised in profiles/spmm_cg_fp32_ch20k_w64.md); None for other shapes
+    # DRAM bytes (read + write) per launch from one ncu capture of this shape; None otherwise
     traffic = _NCU_TRAFFIC.get((args.workload, bv, W))
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -366,18 +383,9 @@ def spmm_roofline(solver, sys_, args, stream, dev) -> dict:
             "peak_source": peaks["source"]}
 
 
-_NCU_TRAFFIC = {("ch20k", 4, 64): 53.08e6}
-
-
-def _atom_blocks(sys_) -> int:
-    atom = sys_.atom_of_row()
-    A = sys_.A
-    first = sys_.orb_offset
-    cnt = 0
-    for I in range(sys_.n_atoms):
-        row = int(first[I])
-        cnt += np.unique(atom[A.indices[A.indptr[row]:A.indptr[row + 1]]]).size
-    return cnt
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# FP32 CG product, one ncu capture per (workload, value bytes, W)
+_NCU_TRAFFIC = {("ch20k", 4, 64): 52.84e6, ("ch100k", 4, 64): 352.84e6}
 
 
 def _peaks() -> dict:

@@ -92,7 +92,7 @@ typedef struct {
   double tol;           /* relative residual ||e_j - (z B - A) x||_2 for every shift; default 1e-8 */
   int32_t max_iter;     /* Lanczos steps per column; default 20000 */
   int32_t batch_w;      /* lanes (columns in flight): 32, 64 or 128; 0 = autotune (default) */
-  int32_t refine;       /* GSK_MIXED only: 1 = FP64 residual correction of each B-solve (default), 0 = none */
+  int32_t refine;       /* mixed modes only: 1 = FP64-accurate residual correction of each B-solve (default), 0 = none */
   int32_t sched;        /* GSK_SCHED_FIFO (default) or GSK_SCHED_LEARNED (model set with gsk_set_sched_model) */
   double inner_tol;     /* relative residual of each B-solve; 0 = default (1e-12 FP64, 3e-6 per FP32 pass) */
   int32_t max_inner;    /* CG iteration cap per B-solve pass; default 200 */
@@ -190,6 +190,54 @@ int gsk_density_noalloc(int64_t n_elem, int32_t n_shifts, const double* eps, con
  * or B (which=1). rho device; result written to *out (host). Synchronous. */
 int gsk_trace(gsk_handle h, int32_t n_cols, const int32_t* cols, const double* rho,
               int32_t which, double* out);
+
+/* Per-shift traces over the column set (Eq. TRACE-X split by shift):
+ *   s[k] = sum_c sum_t Im G[offsets[c]+t][k] * X_{cols[c], i_t},  X = A (which=0) or B (which=1),
+ * where i_t runs over P(cols[c]) in G's layout (gsk_pattern_offsets). With
+ * them Tr(rho X) = -(1/pi) sum_k w_k f(eps_k) s[k] for any mu and kT, so
+ * quantities at several chemical potentials need no second pass over G.
+ *   G   device, offsets[n_cols]*n_shifts complex doubles
+ *   s   host, n_shifts doubles (written)
+ * Synchronous. The order of every sum is fixed (bitwise repeatable). */
+int gsk_shift_trace(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n_shifts,
+                    const double* G, int32_t which, double* s);
+
+/* Chemical potential (Sec. II: mu is set so that the electron count is
+ * reproduced): the mu in [mu_lo, mu_hi] with
+ *   N(mu) = -(1/pi) sum_k w_k f_mu(eps_k) s_k = n_elec,
+ * s_k the per-shift traces with X = B (gsk_shift_trace) and f the Fermi
+ * function of Eq. EQ-FD-FUNC with temperature kT. The search runs on the GPU
+ * (33-section bracketing, to the resolution of FP64); N(mu_lo) < n_elec <=
+ * N(mu_hi) must hold, else GSK_EINVAL (nothing written). If N is not
+ * monotone on the bracket (possible for a column subset), the result is one
+ * of its roots there.
+ *   eps, w  host, n_shifts doubles: Re z_k and quadrature weights
+ *   G       device, as for gsk_shift_trace
+ *   mu      host out; count host out (N(mu)) or NULL
+ * Synchronous. */
+int gsk_find_mu(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n_shifts,
+                const double* eps, const double* w, const double* G, double kT, double n_elec,
+                double mu_lo, double mu_hi, double* mu, double* count);
+
+/* Atom-pair pattern of A in the caller's atom numbering: for atom J,
+ * aidx[aptr[J] .. aptr[J+1]) are the atoms I (ascending) with some A_{Ia,Jb}
+ * in the pattern, J itself included. aptr: host, n_atoms+1 (written);
+ * aidx: host, aptr[n_atoms] entries, or NULL to query the size first. */
+int gsk_atom_pattern(gsk_handle h, int64_t* aptr, int32_t* aidx);
+
+/* Connectivity matrix (Sec. VII, the integrated crystal orbital Hamiltonian
+ * population): C_IJ = sum_a sum_b rho_{Ia;Jb} A_{Jb;Ia}, summed over the
+ * solved columns Jb in cols only, on the atom pattern of gsk_atom_pattern:
+ * C[aptr[J] + s] = C_{aidx[s], J}. Slots of atoms without a column in cols
+ * are 0. Summing C gives Tr(rho A) over the same columns (the electronic
+ * energy when cols covers every row).
+ *   rho   device, laid out like G without the shift axis (gsk_density's output)
+ *   C     device, aptr[n_atoms] doubles (written)
+ *   stream  cudaStream_t or NULL; the gather lists are copied before the
+ *           call returns and the kernel runs asynchronously on that stream.
+ * Each slot sums its terms in a fixed order (bitwise repeatable). */
+int gsk_icohp(gsk_handle h, int32_t n_cols, const int32_t* cols, const double* rho, double* C,
+              void* stream);
 
 /* Library row order: row_lib[i] = row of caller row i in the layout used by
  * gsk_spmm (host array of M entries). */

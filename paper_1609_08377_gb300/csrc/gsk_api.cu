@@ -471,6 +471,7 @@ int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_ha
   L.nbr_roff = h->d_nbr_roff.as<int32_t>();
   L.val_ptr = h->d_val_ptr.as<int64_t>();
   h->atom_perm = std::move(perm);
+  h->atom_of_row = std::move(atom_of_row);
   h->orb_lib = std::move(orb);
   *out = h;
   return GSK_OK;

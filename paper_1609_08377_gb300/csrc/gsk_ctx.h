@@ -52,6 +52,9 @@ struct gsk_ctx {
   std::vector<int8_t> orb_lib;      // library atom -> orbital count
   std::vector<double> pos_lib;      // library atom -> xyz (empty without positions)
   std::vector<double> a_diag, b_diag, a_rowabs, b_rowabs;   // per caller row
+  std::vector<int32_t> atom_of_row;   // caller row -> caller atom
+  std::vector<int64_t> apat_ptr;      // caller atom pattern of A (CSR over atoms; built on first use)
+  std::vector<int32_t> apat_idx;
 
   // device block layout
   gsk::Layout lay{};

@@ -1347,15 +1347,6 @@ struct Launcher {
   }
 };
 
-// Dynamic shared memory of the SpMM kernels (none: the traversal keeps its
-// neighbour blocks in registers and the L1 cache).
-template <typename TV, typename TX, int L>
-constexpr unsigned spmm_smem() { return 0u; }
-template <typename A>
-cudaError_t allow_smem(void (*f)(A), unsigned bytes) {
-  return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
-}
 
 template <int L>
 cudaError_t launch_cg_iteration(const Plan& P, Launcher& la, int pass) {
@@ -1376,10 +1367,10 @@ cudaError_t launch_step_head(const Plan& P, Launcher& la) {
   using K = Kernels<L>;
   const dim3 blk(kThreads);
   if (P.df) {
-    GSK_CUDA_TRY(la(K::spmm_df, dim3(P.grid_rows), blk, P.spAdf, spmm_smem<float2, float2, L>()));
+    GSK_CUDA_TRY(la(K::spmm_df, dim3(P.grid_rows), blk, P.spAdf));
     GSK_CUDA_TRY(la(K::upd_df, dim3(P.grid_vec), blk, P.upd));
   } else {
-    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spA, spmm_smem<double, double, L>()));
+    GSK_CUDA_TRY(la(K::spmm64, dim3(P.grid_rows), blk, P.spA));
     if (!P.mixed)
       GSK_CUDA_TRY(la(K::upd64, dim3(P.grid_vec), blk, P.upd));
     else
@@ -1409,19 +1400,8 @@ cudaError_t launch_step_tail(const Plan& P, Launcher& la) {
 template <int L>
 cudaError_t launch_resid(const Plan& P, Launcher& la) {
   using K = Kernels<L>;
-  if (P.df) return la(K::resid_df, dim3(P.grid_rows), dim3(kThreads), P.spRdf, spmm_smem<float2, float, L>());
-  return la(K::resid, dim3(P.grid_rows), dim3(kThreads), P.spR, spmm_smem<double, float, L>());
-}
-
-template <int L>
-cudaError_t allow_spmm_smem() {
-  using K = Kernels<L>;
-  GSK_CUDA_TRY(allow_smem(K::spmm64, spmm_smem<double, double, L>()));
-  GSK_CUDA_TRY(allow_smem(K::spmm32, spmm_smem<float, float, L>()));
-  GSK_CUDA_TRY(allow_smem(K::resid, spmm_smem<double, float, L>()));
-  GSK_CUDA_TRY(allow_smem(K::spmm_df, spmm_smem<float2, float2, L>()));
-  GSK_CUDA_TRY(allow_smem(K::resid_df, spmm_smem<float2, float, L>()));
-  return cudaSuccess;
+  if (P.df) return la(K::resid_df, dim3(P.grid_rows), dim3(kThreads), P.spRdf);
+  return la(K::resid, dim3(P.grid_rows), dim3(kThreads), P.spR);
 }
 
 // Builds the whole solve as one graph: prime -> WHILE(outer) { head, WHILE(cg1),
@@ -1769,7 +1749,6 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   // ---- run ----
   auto run = [&](auto Ltag) -> cudaError_t {
     constexpr int LL = decltype(Ltag)::value;
-    GSK_CUDA_TRY(allow_spmm_smem<LL>());
     if (opt.use_graph) {
       cudaGraphExec_t ex = nullptr;
       cudaError_t ge = build_graph<LL>(P, &ex);

@@ -73,6 +73,10 @@ def _load() -> C.CDLL:
         "gsk_mlp_train_step": (C.c_int, [I32, P, P, P, P, P, P, I32, C.c_float, P, P, P, P]),
         "gsk_set_sched_model": (C.c_int, [P, P, P]),
         "gsk_autotune": (C.c_int, [P, I32, P, P, I32, P, P, P]),
+        "gsk_shift_trace": (C.c_int, [P, I32, P, I32, P, I32, P]),
+        "gsk_find_mu": (C.c_int, [P, I32, P, I32, P, P, P, D, D, D, D, P, P]),
+        "gsk_atom_pattern": (C.c_int, [P, P, P]),
+        "gsk_icohp": (C.c_int, [P, I32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -144,6 +148,7 @@ class Solver:
         nnz = C.c_int64()
         _check(_lib.gsk_dims(self._h, C.byref(m), C.byref(nnz)), "gsk_dims")
         self.M, self.nnz = int(m.value), int(nnz.value)
+        self.n_atoms = int(off.size)
 
     def _csr(self, X) -> _Csr:
         rp = np.ascontiguousarray(X.indptr, dtype=np.int64)
@@ -242,6 +247,39 @@ class Solver:
         out = C.c_double()
         _check(_lib.gsk_trace(self._h, cols.size, _ptr(cols), _ptr(rho), int(which), C.byref(out)), "gsk_trace")
         return float(out.value)
+
+    def shift_trace(self, cols, n_shifts: int, G, which: int) -> np.ndarray:
+        """gsk_shift_trace: s_k = sum over the columns' patterns of Im G(z_k) X."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        s = np.zeros(int(n_shifts))
+        _check(_lib.gsk_shift_trace(self._h, cols.size, _ptr(cols), int(n_shifts), _ptr(G), int(which),
+                                    _ptr(s)), "gsk_shift_trace")
+        return s
+
+    def find_mu(self, cols, eps, w, G, kT: float, n_elec: float, mu_lo: float, mu_hi: float):
+        """gsk_find_mu: (mu, N(mu)) with N(mu) = n_elec on [mu_lo, mu_hi]."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        mu, cnt = C.c_double(), C.c_double()
+        _check(_lib.gsk_find_mu(self._h, cols.size, _ptr(cols), eps.size, _ptr(eps), _ptr(w), _ptr(G),
+                                float(kT), float(n_elec), float(mu_lo), float(mu_hi), C.byref(mu),
+                                C.byref(cnt)), "gsk_find_mu")
+        return float(mu.value), float(cnt.value)
+
+    def atom_pattern(self):
+        """gsk_atom_pattern: (aptr, aidx) of the atom-pair pattern of A."""
+        aptr = np.zeros(self.n_atoms + 1, dtype=np.int64)
+        _check(_lib.gsk_atom_pattern(self._h, _ptr(aptr), None), "gsk_atom_pattern")
+        aidx = np.zeros(max(int(aptr[-1]), 1), dtype=np.int32)
+        _check(_lib.gsk_atom_pattern(self._h, _ptr(aptr), _ptr(aidx)), "gsk_atom_pattern")
+        return aptr, aidx[:int(aptr[-1])]
+
+    def icohp(self, cols, rho, C_out, stream=None) -> None:
+        """gsk_icohp: C_IJ on the atom pattern (device output C_out)."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        s = getattr(stream, "cuda_stream", stream)
+        _check(_lib.gsk_icohp(self._h, cols.size, _ptr(cols), _ptr(rho), _ptr(C_out), s), "gsk_icohp")
 
 
 def density_noalloc(G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=None) -> None:
