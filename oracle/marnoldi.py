@@ -17,7 +17,9 @@ column vectors G^(j)(z) e_j and rho^(j) e_j are reported on the pattern P(j).
 This module follows those steps plainly:
   1. an orthonormal basis of each Krylov subspace by Arnoldi with Euclidean
      modified Gram-Schmidt, each new vector orthogonalised twice;
-  2. B^-1 e_j by a sparse direct solve;
+  2. B^-1 e_j by conjugate gradients on the SPD B to a 1e-15 relative
+     residual (the oracle's own CG; B is well conditioned, so the solve
+     is accurate to about cond(B) * 1e-15);
   3. an orthonormal basis of the sum: the second basis is projected onto the
      orthogonal complement of the first (twice), and the left singular
      vectors of the result whose singular value -- the sine of a principal
@@ -31,9 +33,9 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as la
-import scipy.sparse.linalg as spla
 
 from .density import fermi
+from .krylov import cg_solve
 
 RANK_TOL = 1e-7      # smallest sine of a principal angle kept between the two Krylov subspaces
 
@@ -72,20 +74,20 @@ def principal_sines(A, B, j: int, nu: int) -> np.ndarray:
     e = np.zeros(M)
     e[j] = 1.0
     Q1 = krylov_basis(A, e, nu // 2)
-    Q2 = krylov_basis(A, spla.spsolve(B.tocsc(), e), nu // 2)
+    Q2 = krylov_basis(A, cg_solve(B, e, 1e-15), nu // 2)
     for _ in range(2):
         Q2 = Q2 - Q1 @ (Q1.T @ Q2)
     return np.sort(np.linalg.svd(Q2, compute_uv=False))
 
 
-def subspace_basis(A, B, j: int, nu: int, rank_tol: float = RANK_TOL) -> np.ndarray:
+def subspace_basis(A, B, j: int, nu: int, rank_tol: float = RANK_TOL, seed_tol: float = 1e-15) -> np.ndarray:
     """Orthonormal basis of K_{nu/2}(A; e_j) + K_{nu/2}(A; B^-1 e_j) (Eq. EQ-LS-MULTIPLE)."""
     if nu < 2 or nu % 2:
         raise ValueError("nu must be even and >= 2")
     M = A.shape[0]
     e = np.zeros(M)
     e[j] = 1.0
-    binv_e = spla.spsolve(B.tocsc(), e)
+    binv_e = cg_solve(B, e, seed_tol)
     Q1 = krylov_basis(A, e, nu // 2)
     Q2 = krylov_basis(A, binv_e, nu // 2)
     for _ in range(2):
@@ -96,9 +98,10 @@ def subspace_basis(A, B, j: int, nu: int, rank_tol: float = RANK_TOL) -> np.ndar
     return np.hstack([Q1, U[:, s >= rank_tol]])
 
 
-def ritz_pairs(A, B, j: int, nu: int, rank_tol: float = RANK_TOL):
-    """(eps, V): Ritz values (ascending) and B-orthonormal Ritz vectors (M x r)."""
-    Q = subspace_basis(A, B, j, nu, rank_tol)
+def ritz_pairs(A, B, j: int, nu: int, rank_tol: float = RANK_TOL, seed_tol: float = 1e-15):
+    """(eps, V): Ritz values (ascending) and B-orthonormal Ritz vectors (M x r).
+    seed_tol is the relative CG residual of B^-1 e_j."""
+    Q = subspace_basis(A, B, j, nu, rank_tol, seed_tol)
     At = Q.T @ (A @ Q)
     Bt = Q.T @ (B @ Q)
     At = (At + At.T) / 2
@@ -108,7 +111,7 @@ def ritz_pairs(A, B, j: int, nu: int, rank_tol: float = RANK_TOL):
 
 
 def marnoldi_column(A, B, j: int, nu: int, z=None, mu: float = 0.0, kT: float = 0.1,
-                    rank_tol: float = RANK_TOL):
+                    rank_tol: float = RANK_TOL, seed_tol: float = 1e-15):
     """Outputs for column j on its pattern P(j) (rows of CSR row j of A, in order):
 
       eps    Ritz values (r,)
@@ -117,7 +120,7 @@ def marnoldi_column(A, B, j: int, nu: int, z=None, mu: float = 0.0, kT: float = 
       w      the weights (v_m)_j (v_m)_j, so that rho_jj = sum_m f(eps_m) w_m
       q      the charges (v_m)_j (B v_m)_j, so that e_j^T rho B e_j = sum_m f(eps_m) q_m
     """
-    eps, V = ritz_pairs(A, B, j, nu, rank_tol)
+    eps, V = ritz_pairs(A, B, j, nu, rank_tol, seed_tol)
     rows = A.indices[A.indptr[j]:A.indptr[j + 1]]
     vj = V[j, :]
     f = fermi(eps, mu, kT)
