@@ -239,6 +239,37 @@ int gsk_atom_pattern(gsk_handle h, int64_t* aptr, int32_t* aidx);
 int gsk_icohp(gsk_handle h, int32_t n_cols, const int32_t* cols, const double* rho, double* C,
               void* stream);
 
+/* Multiple Arnoldi projection (Sec. III-B, Eq. EQ-LS-MULTIPLE,
+ * EQ-EIG-GREEN-KRYLOV, EQ-PROJ-PHYS-QUANT-KRYLOV): for each column j the
+ * pencil is projected onto K_{nu/2}(A; e_j) + K_{nu/2}(A; B^-1 e_j); the
+ * reduced problem gives Ritz values eps_m and B-orthonormal Ritz vectors v_m,
+ * and the energy integral is done analytically:
+ *   rho_ij    = sum_m f(eps_m) (v_m)_i (v_m)_j                 i in P(j)
+ *   G_ij(z_k) = sum_m (v_m)_i (v_m)_j / (z_k - eps_m)           (optional)
+ * This is the paper's own approximation, not the exact-to-tolerance solve
+ * of gsk_solve: it is exact when nu/2 reaches the dimension of the Krylov
+ * space of e_j. Directions of the second subspace within sin(theta) < 1e-7 of
+ * the first are dropped, and a Krylov sequence ends early where it becomes
+ * invariant (new direction below 1e-13 ||A||_inf), so the rank r can be
+ * below nu.
+ *   nu       even, 2 .. GSK_MA_MAX_NU
+ *   mu, kT   Fermi function of Eq. EQ-FD-FUNC (kT > 0)
+ *   rho      device, offsets[n_cols] doubles, G's layout without the shift axis
+ *   n_shifts 0, or S >= 1 with z (host, 2*S doubles: re, im) and G (device,
+ *            offsets[n_cols]*S complex doubles, as for gsk_solve)
+ *   ritz     host, n_cols*nu doubles or NULL: eps_m ascending, NaN past r
+ *   weight   host, n_cols*nu doubles or NULL: (v_m)_j^2 (rho_jj = sum f w)
+ *   charge   host, n_cols*nu doubles or NULL: (v_m)_j (B v_m)_j; their sum
+ *            is 1 for every column (e_j lies in the subspace)
+ *   rank     host, n_cols or NULL: r, or -1 if Q^T B Q was not positive
+ *            definite (the column's outputs are then not meaningful)
+ * Columns run in batches of 32 on FP64 arithmetic. Synchronous. Returns
+ * GSK_ETIMEOUT if the CG for B^-1 e_j did not reach 1e-15 in 2000 steps. */
+#define GSK_MA_MAX_NU 32
+int gsk_marnoldi(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t nu, double mu, double kT,
+                 double* rho, int32_t n_shifts, const double* z, double* G, double* ritz, double* weight,
+                 double* charge, int32_t* rank);
+
 /* Library row order: row_lib[i] = row of caller row i in the layout used by
  * gsk_spmm (host array of M entries). */
 int gsk_row_order(gsk_handle h, int32_t* row_lib);

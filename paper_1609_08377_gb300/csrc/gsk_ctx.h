@@ -81,11 +81,12 @@ struct gsk_ctx {
   gsk::DevBuf ws_gstage;   // staging of G for host output buffers
   gsk::DevBuf ws_misc;     // density / trace scratch
   gsk::DevBuf ws_tune;     // G of the autotuner's truncated solves
+  gsk::DevBuf ws_ma;       // multiple Arnoldi: vectors, Grams, small matrices
 
   ~gsk_ctx() {
     gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr, &d_warp_atoms,
                           &d_A64, &d_B64, &d_A32, &d_B32, &d_A2, &d_B2, &ws_vec, &ws_lane, &ws_jobs,
-                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune};
+                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune, &ws_ma};
     for (auto* b : all) b->release();
   }
 };
@@ -102,4 +103,6 @@ int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int
                   const gsk_options* opt, int32_t* best_w);
 int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
               void* stream);
+size_t spmm64_ws_bytes(const gsk_ctx* h);
+int spmm64_dot(gsk_ctx* h, int which, int W, const double* X, double* Y, double* dots, void* ws, cudaStream_t s);
 }

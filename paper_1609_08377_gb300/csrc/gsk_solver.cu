@@ -1873,6 +1873,41 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
   return GSK_OK;
 }
 
+// Bytes of the reduction workspace that spmm64_dot needs (zero it once
+// before the first call; its counters are reset by their last user).
+size_t spmm64_ws_bytes(const gsk_ctx* h) {
+  const int n_grp_max = (kMaxRedCtas + kRedGroup - 1) / kRedGroup;
+  return 256 + (size_t)h->lay.n_ctas * kMaxW * sizeof(double) + (size_t)n_grp_max * kMaxW * sizeof(double) +
+         n_grp_max * sizeof(unsigned) + 256;
+}
+
+// Y = S X on W = 32 or 64 FP64 lanes (S = A for which = 0, B for which = 1)
+// with the per-lane dot X.Y written to dots[0..W) (device): the solver's
+// block SpMM kernel in its plain-product form, for callers outside the
+// shifted solve (the multiple Arnoldi path).
+int spmm64_dot(gsk_ctx* h, int which, int W, const double* X, double* Y, double* dots, void* ws, cudaStream_t s) {
+  if ((W != 32 && W != 64) || !X || !Y || !dots || !ws) return GSK_EINVAL;
+  const int grid = h->lay.n_ctas;
+  if (grid > kMaxRedCtas) return GSK_ENOTSUP;
+  const int n_grp_max = (kMaxRedCtas + kRedGroup - 1) / kRedGroup;
+  char* b = static_cast<char*>(ws);
+  LaneCtl c{};
+  c.red_out = dots;
+  c.red_counter = reinterpret_cast<unsigned int*>(b);
+  c.partials = reinterpret_cast<double*>(b + 256);
+  c.grp_partials = c.partials + (size_t)grid * kMaxW;
+  c.grp_counter = reinterpret_cast<unsigned int*>(c.grp_partials + (size_t)n_grp_max * kMaxW);
+  RedArgs r{};
+  r.c = c;
+  r.fin = FIN_SUM;
+  r.W = W;
+  SpmmArgs<double, double, double> a{h->lay, (which ? h->d_B64 : h->d_A64).as<double>(), X, Y,
+                                     nullptr, nullptr, nullptr, r};
+  if (W == 32) k_spmm<double, double, double, double, 1, SP_DOT><<<grid, kThreads, 0, s>>>(a);
+  else k_spmm<double, double, double, double, 2, SP_DOT><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? GSK_OK : GSK_ECUDA;
+}
+
 }  // namespace gsk
 
 namespace gsk {

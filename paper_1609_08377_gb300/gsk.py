@@ -77,6 +77,7 @@ def _load() -> C.CDLL:
         "gsk_find_mu": (C.c_int, [P, I32, P, I32, P, P, P, D, D, D, D, P, P]),
         "gsk_atom_pattern": (C.c_int, [P, P, P]),
         "gsk_icohp": (C.c_int, [P, I32, P, P, P, P]),
+        "gsk_marnoldi": (C.c_int, [P, I32, P, I32, D, D, P, I32, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -274,6 +275,25 @@ class Solver:
         aidx = np.zeros(max(int(aptr[-1]), 1), dtype=np.int32)
         _check(_lib.gsk_atom_pattern(self._h, _ptr(aptr), _ptr(aidx)), "gsk_atom_pattern")
         return aptr, aidx[:int(aptr[-1])]
+
+    def marnoldi(self, cols, nu: int, mu: float, kT: float, rho, z=None, G=None):
+        """gsk_marnoldi: multiple Arnoldi rho (and G at shifts z) on the columns'
+        patterns; returns (ritz, weight, charge, rank) as host arrays."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        n = cols.size
+        ritz = np.zeros(max(n * nu, 1))
+        weight = np.zeros(max(n * nu, 1))
+        charge = np.zeros(max(n * nu, 1))
+        rank = np.zeros(max(n, 1), dtype=np.int32)
+        if z is None:
+            zz, S = None, 0
+        else:
+            zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).view(np.float64))
+            S = zz.size // 2
+        _check(_lib.gsk_marnoldi(self._h, n, _ptr(cols), int(nu), float(mu), float(kT), _ptr(rho), S, _ptr(zz),
+                                 _ptr(G), _ptr(ritz), _ptr(weight), _ptr(charge), _ptr(rank)), "gsk_marnoldi")
+        sh = (n, nu)
+        return ritz[:n * nu].reshape(sh), weight[:n * nu].reshape(sh), charge[:n * nu].reshape(sh), rank[:n]
 
     def icohp(self, cols, rho, C_out, stream=None) -> None:
         """gsk_icohp: C_IJ on the atom pattern (device output C_out)."""
