@@ -161,9 +161,10 @@ __global__ void k_gram_fold(int n_chunks, int n_out, const double* __restrict__ 
   }
 }
 
-// Z_b[r, c] = beta * Y_b[r, c] + gamma * sum_a X_a[r, c] * K[(a * nz + b) * C + c].
-// One thread per (row, column); it reads every X_a of its element before it
-// writes, so Z may alias X or Y element for element.
+// Z_b[r, c] = beta * Y_b[r, c] + gamma * sum_a X_a[r, c] * K[(a * nz + b) * C + c],
+// for nx <= NX. One thread per (row, column); it reads every X_a of its
+// element before it writes, so Z may alias X or Y element for element.
+template <int NX>
 __global__ void __launch_bounds__(256) k_combine(VecSet X, VecSet Y, VecSetW Z, const double* __restrict__ K,
                                                  int C, int M, double beta, double gamma) {
   const int64_t total = (int64_t)M * C;
@@ -172,13 +173,13 @@ __global__ void __launch_bounds__(256) k_combine(VecSet X, VecSet Y, VecSetW Z, 
        t += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(t % C);
     const size_t r = (size_t)(t / C);
-    double x[kMaxN];
+    double x[NX];
 #pragma unroll
-    for (int a = 0; a < kMaxN; ++a) x[a] = a < nx ? X.p[a][r * X.ld + X.off[a] + c] : 0.0;
+    for (int a = 0; a < NX; ++a) x[a] = a < nx ? X.p[a][r * X.ld + X.off[a] + c] : 0.0;
     for (int b = 0; b < nz; ++b) {
       double s = 0.0;
 #pragma unroll
-      for (int a = 0; a < kMaxN; ++a)
+      for (int a = 0; a < NX; ++a)
         if (a < nx) s = fma(x[a], K[(size_t)(a * nz + b) * C + c], s);
       double v = gamma * s;
       if (beta != 0.0) v = fma(beta, Y.p[b][r * Y.ld + Y.off[b] + c], v);
@@ -300,8 +301,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Cyclic Jacobi (row-by-row pair order): each rotation J(p, q) zeroing H[p][q]
 // is computed by every lane from the same three entries and applied as
 // H <- J^T H J (rows p, q, then columns p, q) and Z <- Z J, lane x taking
-// element x. Sweeps stop when the off-diagonal mass is below 1e-30 of the
-// total, or after kMaxSweeps.
+// element x; an off-diagonal below 1e-17 sqrt|H_pp H_qq| is set to zero
+// instead (threshold Jacobi). Sweeps stop when the off-diagonal mass is below
+// 1e-30 of the total, or after kMaxSweeps.
 __device__ void warp_jacobi(double (*H)[kLD], double (*Z)[kLD], int n) {
   const int lane = threadIdx.x & 31;
   for (int i = 0; i < n; ++i)
@@ -321,9 +323,20 @@ __device__ void warp_jacobi(double (*H)[kLD], double (*Z)[kLD], int n) {
     if (!(off > 1e-30 * tot)) break;
     for (int p = 0; p < n - 1; ++p) {
       for (int q = p + 1; q < n; ++q) {
-        const double apq = H[p][q];
-        if (apq == 0.0) continue;                 // the same value in every lane
-        const double tau = (H[q][q] - H[p][p]) / (2.0 * apq);
+        const double apq = H[p][q];               // the same values in every lane
+        const double app = H[p][p], aqq = H[q][q];
+        if (apq == 0.0) continue;
+        if (fabs(apq) <= 1e-17 * sqrt(fabs(app * aqq))) {
+          // negligible: setting it to zero moves the eigenvalues by O(apq^2 / gap)
+          __syncwarp();
+          if (lane == 0) {
+            H[p][q] = 0.0;
+            H[q][p] = 0.0;
+          }
+          __syncwarp();
+          continue;
+        }
+        const double tau = (aqq - app) / (2.0 * apq);
         const double t = fabs(tau) > 1e150 ? 0.5 / tau
                                             : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
         const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
@@ -643,7 +656,12 @@ struct Runner {
   }
   void combine(const VecSet& X, const VecSet& Y, const VecSetW& Z, const double* K, int C, double beta,
                double gamma) {
-    k_combine<<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
+    if (X.n <= 1) k_combine<1><<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
+    else if (X.n <= 2) k_combine<2><<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
+    else if (X.n <= 4) k_combine<4><<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
+    else if (X.n <= 8) k_combine<8><<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
+    else if (X.n <= 16) k_combine<16><<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
+    else k_combine<kMaxN><<<grid_vec, 256>>>(X, Y, Z, K, C, M, beta, gamma);
     ok = ok && cudaGetLastError() == cudaSuccess;
   }
 };
