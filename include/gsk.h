@@ -219,6 +219,13 @@ int gsk_find_mu(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n_shi
                 const double* eps, const double* w, const double* G, double kT, double n_elec,
                 double mu_lo, double mu_hi, double* mu, double* count);
 
+/* The same chemical-potential search from per-shift traces the caller
+ * already has (host, n_shifts doubles: s_k with X = B, e.g. gsk_shift_trace
+ * results summed over the ranks that share the column set). N(mu), the
+ * bracket rule and the outputs are as for gsk_find_mu. Synchronous. */
+int gsk_mu_from_traces(gsk_handle h, int32_t n_shifts, const double* eps, const double* w, const double* s,
+                       double kT, double n_elec, double mu_lo, double mu_hi, double* mu, double* count);
+
 /* Atom-pair pattern of A in the caller's atom numbering: for atom J,
  * aidx[aptr[J] .. aptr[J+1]) are the atoms I (ascending) with some A_{Ia,Jb}
  * in the pattern, J itself included. aptr: host, n_atoms+1 (written);

@@ -222,20 +222,10 @@ int gsk_shift_trace(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n
              ? GSK_OK : GSK_ECUDA;
 }
 
-int gsk_find_mu(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n_shifts, const double* eps,
-                const double* w, const double* G, double kT, double n_elec, double mu_lo, double mu_hi,
-                double* mu, double* count) {
-  if (!h || n_cols < 1 || !cols || n_shifts < 1 || !eps || !w || !G || !mu) return GSK_EINVAL;
-  if (!(kT > 0.0) || !isfinite(kT) || !isfinite(n_elec) || !isfinite(mu_lo) || !isfinite(mu_hi) ||
-      !(mu_lo < mu_hi))
-    return GSK_EINVAL;
-  if (!finite_n(eps, n_shifts) || !finite_n(w, n_shifts) || !cols_valid(h, n_cols, cols)) return GSK_EINVAL;
-  if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
-  char* d_front = nullptr;
-  double* d_s = nullptr;
-  const size_t front = (2 * (size_t)n_shifts + 4) * sizeof(double);
-  const int rc = shift_trace_device(h, n_cols, cols, n_shifts, G, 1, front, &d_front, &d_s);
-  if (rc != GSK_OK) return rc;
+// mu search on the GPU from per-shift traces already in device memory
+// (d_front holds room for eps, w and the 3 outputs, d_s the traces).
+static int mu_search_device(int32_t n_shifts, const double* eps, const double* w, const double* d_s, char* d_front,
+                            double kT, double n_elec, double mu_lo, double mu_hi, double* mu, double* count) {
   double* d_eps = reinterpret_cast<double*>(d_front);
   double* d_w = d_eps + n_shifts;
   double* d_out = d_w + n_shifts;
@@ -251,6 +241,42 @@ int gsk_find_mu(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n_shi
   *mu = out[0];
   if (count) *count = out[1];
   return GSK_OK;
+}
+
+static bool mu_args_ok(int32_t n_shifts, const double* eps, const double* w, double kT, double n_elec, double mu_lo,
+                       double mu_hi, const double* mu) {
+  if (n_shifts < 1 || !eps || !w || !mu) return false;
+  if (!(kT > 0.0) || !isfinite(kT) || !isfinite(n_elec) || !isfinite(mu_lo) || !isfinite(mu_hi) || !(mu_lo < mu_hi))
+    return false;
+  return finite_n(eps, n_shifts) && finite_n(w, n_shifts);
+}
+
+int gsk_mu_from_traces(gsk_handle h, int32_t n_shifts, const double* eps, const double* w, const double* s,
+                       double kT, double n_elec, double mu_lo, double mu_hi, double* mu, double* count) {
+  if (!h || !s || !mu_args_ok(n_shifts, eps, w, kT, n_elec, mu_lo, mu_hi, mu)) return GSK_EINVAL;
+  if (!finite_n(s, n_shifts)) return GSK_EINVAL;
+  if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
+  const size_t front = align256((2 * (size_t)n_shifts + 4) * sizeof(double));
+  if (h->ws_misc.ensure(front + (size_t)n_shifts * sizeof(double)) != cudaSuccess) return GSK_ENOMEM;
+  char* base = h->ws_misc.as<char>();
+  double* d_s = reinterpret_cast<double*>(base + front);
+  if (cudaMemcpy(d_s, s, (size_t)n_shifts * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return GSK_ECUDA;
+  return mu_search_device(n_shifts, eps, w, d_s, base, kT, n_elec, mu_lo, mu_hi, mu, count);
+}
+
+int gsk_find_mu(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t n_shifts, const double* eps,
+                const double* w, const double* G, double kT, double n_elec, double mu_lo, double mu_hi,
+                double* mu, double* count) {
+  if (!h || n_cols < 1 || !cols || !G || !mu_args_ok(n_shifts, eps, w, kT, n_elec, mu_lo, mu_hi, mu))
+    return GSK_EINVAL;
+  if (!cols_valid(h, n_cols, cols)) return GSK_EINVAL;
+  if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
+  char* d_front = nullptr;
+  double* d_s = nullptr;
+  const size_t front = (2 * (size_t)n_shifts + 4) * sizeof(double);
+  const int rc = shift_trace_device(h, n_cols, cols, n_shifts, G, 1, front, &d_front, &d_s);
+  if (rc != GSK_OK) return rc;
+  return mu_search_device(n_shifts, eps, w, d_s, d_front, kT, n_elec, mu_lo, mu_hi, mu, count);
 }
 
 int gsk_atom_pattern(gsk_handle h, int64_t* aptr, int32_t* aidx) {

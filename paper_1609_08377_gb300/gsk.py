@@ -78,6 +78,7 @@ def _load() -> C.CDLL:
         "gsk_atom_pattern": (C.c_int, [P, P, P]),
         "gsk_icohp": (C.c_int, [P, I32, P, P, P, P]),
         "gsk_marnoldi": (C.c_int, [P, I32, P, I32, D, D, P, I32, P, P, P, P, P, P]),
+        "gsk_mu_from_traces": (C.c_int, [P, I32, P, P, P, D, D, D, D, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -266,6 +267,16 @@ class Solver:
         _check(_lib.gsk_find_mu(self._h, cols.size, _ptr(cols), eps.size, _ptr(eps), _ptr(w), _ptr(G),
                                 float(kT), float(n_elec), float(mu_lo), float(mu_hi), C.byref(mu),
                                 C.byref(cnt)), "gsk_find_mu")
+        return float(mu.value), float(cnt.value)
+
+    def mu_from_traces(self, eps, w, s, kT: float, n_elec: float, mu_lo: float, mu_hi: float):
+        """gsk_mu_from_traces: (mu, N(mu)) from per-shift traces s (host)."""
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        mu, cnt = C.c_double(), C.c_double()
+        _check(_lib.gsk_mu_from_traces(self._h, eps.size, _ptr(eps), _ptr(w), _ptr(s), float(kT), float(n_elec),
+                                       float(mu_lo), float(mu_hi), C.byref(mu), C.byref(cnt)), "gsk_mu_from_traces")
         return float(mu.value), float(cnt.value)
 
     def atom_pattern(self):

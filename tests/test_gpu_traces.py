@@ -123,3 +123,23 @@ def test_icohp_matches_oracle(gsk, n_cols):
     assert np.abs(got - want).max() <= 1e-13 * max(1.0, np.abs(want).max())
     assert np.isclose(got.sum(), solver.trace(cols, _dev(rho), 0), rtol=1e-12)
     solver.close()
+
+
+def test_mu_from_traces_matches_find_mu(gsk):
+    """gsk_mu_from_traces on the summed traces of two column halves (what the
+    ranks of a sharded run exchange) gives the mu of gsk_find_mu on all columns."""
+    from paper_1609_08377_gb300 import sharding
+
+    s, cols, eps, w, z, G, off = _case(64, 1.0, 1, 64)
+    solver = gsk.from_system(s)
+    kT, n_elec = 0.3, 0.4 * density.count_from_traces(density.shift_traces(G, s.B, cols, off), eps, w, 50.0, 0.3)
+    mu_all, cnt_all = solver.find_mu(cols, eps, w, _dev(G), kT, n_elec, -40.0, 40.0)
+    halves = [sharding.shard_columns(cols, r, 2) for r in range(2)]
+    s_sum = np.zeros(eps.size)
+    for h in halves:
+        Gh = dense.green_lu(s.A, s.B, z, h)
+        s_sum += solver.shift_trace(h, eps.size, _dev(Gh), 1)
+    mu, cnt = solver.mu_from_traces(eps, w, s_sum, kT, n_elec, -40.0, 40.0)
+    assert abs(mu - mu_all) <= 1e-11 * max(1.0, abs(mu_all))
+    assert abs(cnt - n_elec) <= 1e-11 * n_elec
+    solver.close()
