@@ -17,6 +17,8 @@ Modules:
              pattern by quadrature of Eq. EQ-DM-GREEN-FN; per-shift traces,
              the chemical potential for an electron count (bisection) and
              the ICOHP connectivity C_IJ (Sec. VII).
+  projection-- the real-space projection of one column (Sec. III-B): the
+             kappa-atom region, the restricted pencil, multiple Arnoldi on it.
   marnoldi-- the multiple Arnoldi projection of one column (Sec. III-B,
              Eq. EQ-LS-MULTIPLE): Ritz pairs of the pencil on
              K(A; e_j) + K(A; B^-1 e_j), G^(j) and rho^(j) by the analytic
