@@ -277,6 +277,26 @@ int gsk_marnoldi(gsk_handle h, int32_t n_cols, const int32_t* cols, int32_t nu, 
                  double* rho, int32_t n_shifts, const double* z, double* G, double* ritz, double* weight,
                  double* charge, int32_t* rank);
 
+/* Real-space projection (Sec. III-B): column j is solved on the pencil
+ * restricted to the orbitals of the region around its atom J -- every atom
+ * within the distance of J's kappa-th nearest atom (J counted, ties kept),
+ * so the region holds kappa atoms or more -- by the multiple Arnoldi
+ * projection of gsk_marnoldi (same nu, mu, kT, outputs and conventions, with
+ * ritz/weight/charge/rank of the projected problem). Distances use the
+ * positions given to gsk_create (required; GSK_EINVAL without them) and the
+ * minimum-image convention in the periodic box (Lx, Ly, Lz) when box is not
+ * NULL.
+ *   rho      device, the layout of gsk_pattern_offsets without the shift
+ *            axis; entries whose row lies outside the region are 0
+ *   m_local  host, n_cols or NULL: orbitals in each column's region (M')
+ * The regions are found and the restricted pencils assembled on the host
+ * (a batch of 32 columns becomes one block-diagonal pencil solved on the
+ * GPU). On first use the matrix values are copied back to the host once.
+ * Synchronous. */
+int gsk_marnoldi_projected(gsk_handle h, const double* box, int32_t kappa, int32_t n_cols, const int32_t* cols,
+                           int32_t nu, double mu, double kT, double* rho, double* ritz, double* weight,
+                           double* charge, int32_t* rank, int32_t* m_local);
+
 /* Library row order: row_lib[i] = row of caller row i in the layout used by
  * gsk_spmm (host array of M entries). */
 int gsk_row_order(gsk_handle h, int32_t* row_lib);

@@ -55,6 +55,9 @@ struct gsk_ctx {
   std::vector<int32_t> atom_of_row;   // caller row -> caller atom
   std::vector<int64_t> apat_ptr;      // caller atom pattern of A (CSR over atoms; built on first use)
   std::vector<int32_t> apat_idx;
+  std::vector<double> host_A64, host_B64;   // block-layout values on the host (projection; on first use)
+  std::vector<double> pos_caller;          // caller-order positions (projection; on first use)
+  std::vector<int32_t> atom_first_row;     // first row of every caller atom, and M (projection)
 
   // device block layout
   gsk::Layout lay{};
@@ -82,11 +85,12 @@ struct gsk_ctx {
   gsk::DevBuf ws_misc;     // density / trace scratch
   gsk::DevBuf ws_tune;     // G of the autotuner's truncated solves
   gsk::DevBuf ws_ma;       // multiple Arnoldi: vectors, Grams, small matrices
+  gsk::DevBuf ws_proj;     // real-space projection: local rho and scatter map
 
   ~gsk_ctx() {
     gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr, &d_warp_atoms,
                           &d_A64, &d_B64, &d_A32, &d_B32, &d_A2, &d_B2, &ws_vec, &ws_lane, &ws_jobs,
-                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune, &ws_ma};
+                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune, &ws_ma, &ws_proj};
     for (auto* b : all) b->release();
   }
 };

@@ -79,6 +79,7 @@ def _load() -> C.CDLL:
         "gsk_icohp": (C.c_int, [P, I32, P, P, P, P]),
         "gsk_marnoldi": (C.c_int, [P, I32, P, I32, D, D, P, I32, P, P, P, P, P, P]),
         "gsk_mu_from_traces": (C.c_int, [P, I32, P, P, P, D, D, D, D, P, P]),
+        "gsk_marnoldi_projected": (C.c_int, [P, P, I32, I32, P, I32, D, D, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -305,6 +306,24 @@ class Solver:
                                  _ptr(G), _ptr(ritz), _ptr(weight), _ptr(charge), _ptr(rank)), "gsk_marnoldi")
         sh = (n, nu)
         return ritz[:n * nu].reshape(sh), weight[:n * nu].reshape(sh), charge[:n * nu].reshape(sh), rank[:n]
+
+    def marnoldi_projected(self, cols, kappa: int, nu: int, mu: float, kT: float, rho, box=None):
+        """gsk_marnoldi_projected: multiple Arnoldi on each column's kappa-atom
+        region; returns (ritz, weight, charge, rank, m_local) as host arrays."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        n = cols.size
+        ritz = np.zeros(max(n * nu, 1))
+        weight = np.zeros(max(n * nu, 1))
+        charge = np.zeros(max(n * nu, 1))
+        rank = np.zeros(max(n, 1), dtype=np.int32)
+        m_local = np.zeros(max(n, 1), dtype=np.int32)
+        bx = None if box is None else np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+        _check(_lib.gsk_marnoldi_projected(self._h, _ptr(bx), int(kappa), n, _ptr(cols), int(nu), float(mu),
+                                           float(kT), _ptr(rho), _ptr(ritz), _ptr(weight), _ptr(charge),
+                                           _ptr(rank), _ptr(m_local)), "gsk_marnoldi_projected")
+        sh = (n, nu)
+        return (ritz[:n * nu].reshape(sh), weight[:n * nu].reshape(sh), charge[:n * nu].reshape(sh), rank[:n],
+                m_local[:n])
 
     def icohp(self, cols, rho, C_out, stream=None) -> None:
         """gsk_icohp: C_IJ on the atom pattern (device output C_out)."""
