@@ -42,7 +42,7 @@ extern "C" {
 #define GSK_ENOMEM (-3)     /* device or host allocation failed */
 #define GSK_ECUDA (-4)      /* a CUDA runtime call failed */
 #define GSK_ETIMEOUT (-5)   /* a bounded device wait gave up */
-#define GSK_ENOTSUP (-6)    /* option combination not supported by this build */
+#define GSK_ENOTSUP (-6)    /* option combination not supported (e.g. FP64 with 128 lanes) */
 
 /* ----- per-column status codes (status[] of gsk_solve) -------------------- */
 #define GSK_CONVERGED 0      /* every shift reached the residual tolerance */
