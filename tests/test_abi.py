@@ -98,3 +98,33 @@ def test_create_rejects_bad_inputs_on_host(libgsk):
     # different patterns
     Bd = sp.csr_matrix(np.eye(8))
     assert _create(libgsk, A, Bd, off, cnt) == libgsk.GSK_EINVAL
+
+
+def _prototypes(header):
+    """name -> number of parameters of every function prototype in a header."""
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for m in re.finditer(r"\b(gsk_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header(libgsk):
+    """Every function the Python binding declares has the parameter count of
+    its prototype in include/gsk.h (a mismatch would pass garbage through
+    ctypes without any error)."""
+    from paper_1609_08377_gb300 import gsk as g
+
+    protos = _prototypes("gsk.h")
+    lib = g.lib()
+    checked = 0
+    for name, proto_n in protos.items():
+        f = getattr(lib, name)
+        if f.argtypes is None:
+            continue
+        assert len(f.argtypes) == proto_n, (name, len(f.argtypes), proto_n)
+        checked += 1
+    assert checked >= 25
