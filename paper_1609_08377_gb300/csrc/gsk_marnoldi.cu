@@ -644,6 +644,10 @@ struct Runner {
     const int rows = (M + chunks - 1) / chunks;
     chunks = (M + rows - 1) / rows;
     const int n_ent = kGramCols * X.n * Y.n;
+    if (n_ent > kGramAcc * kGramThreads) {                // more entries than the widest variant holds
+      ok = false;
+      return;
+    }
     const dim3 grid(chunks, groups);
     if (n_ent <= kGramThreads) k_gram<1><<<grid, kGramThreads>>>(X, Y, M, C, rows, part);
     else if (n_ent <= 2 * kGramThreads) k_gram<2><<<grid, kGramThreads>>>(X, Y, M, C, rows, part);

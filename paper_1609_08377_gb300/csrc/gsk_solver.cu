@@ -1317,7 +1317,6 @@ struct Kernels {
   static constexpr auto dot64 = k_dot_uv<double, L, false>;
   static constexpr auto fin64 = k_finish<double, L, false>;
   // mixed mode
-  static constexpr auto spmm32 = k_spmm<float, float, float, float, L, SP_DOT>;
   static constexpr auto spmm32cg = k_spmm<float, float, float, float, L, SP_CG>;
   static constexpr auto resid = k_spmm<double, float, float, double, L, SP_RESID>;
   static constexpr auto upd32 = k_update<float, L>;
