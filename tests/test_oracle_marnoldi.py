@@ -171,3 +171,20 @@ def test_analytic_integral_matches_quadrature(c64):
     f = density.fermi(eps_r, mu, kT)
     assert np.all(np.abs(quad - o["rho"]) <= np.abs(c) @ np.abs(F - f) + 1e-8)
     assert np.abs(F - f).max() < 0.05       # the smoothing is a small correction at eta = 0.01
+
+
+@pytest.mark.parametrize("mu,kT", [(-10.0, 0.1), (-2.0, 0.5), (5.0, 0.05)])
+def test_rho_trace_equals_weighted_charges(c64, mu, kT):
+    """e_j^T rho^(j) B e_j two ways (Eq. EQ-PROJ-PHYS-QUANT-KRYLOV with X = B):
+    through rho on the pattern, sum_i rho_ij B_ij, and through the Ritz
+    charges, sum_m f(eps_m) (v_m)_j (B v_m)_j; and with X = A the energy
+    sum_i rho_ij A_ij equals sum_m f(eps_m) eps_m (v_m)_j (B v_m)_j."""
+    A, B = c64.A, c64.B
+    for j in (2, 64, 200):
+        o = ma.marnoldi_column(A, B, j, 30, mu=mu, kT=kT)
+        lo, hi = A.indptr[j], A.indptr[j + 1]
+        f = density.fermi(o["eps"], mu, kT)
+        via_rho_B = float(o["rho"] @ B.data[lo:hi])
+        via_rho_A = float(o["rho"] @ A.data[lo:hi])
+        assert abs(via_rho_B - f @ o["q"]) <= 1e-12 * max(1.0, abs(via_rho_B))
+        assert abs(via_rho_A - (f * o["eps"]) @ o["q"]) <= 1e-11 * max(1.0, abs(via_rho_A))
