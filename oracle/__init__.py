@@ -12,7 +12,10 @@ Modules:
              eigendecomposition closed form (Eq. EQ-EIG-GREEN).
   krylov  -- O3: naive B-inner-product Lanczos with tridiagonal solves per
              shift (Sec. III-B, shared Krylov subspace for all shifts);
-             O3': plain COCG on z B - A, one shift at a time.
+             O3': plain COCG on z B - A, one shift at a time;
+             lanczos_batch: O3 over a batch of columns, whose sparse
+             products, CG solves and pivoted tridiagonal solves run in
+             plain C with OpenMP (o3_batch.c, built by build_c.py).
   density -- Fermi function (Eq. EQ-FD-FUNC) and the density matrix on the
              pattern by quadrature of Eq. EQ-DM-GREEN-FN; per-shift traces,
              the chemical potential for an electron count (bisection) and

@@ -197,3 +197,166 @@ def cocg_solve(A, B, j: int, zk: complex, tol: float = 1e-12, max_iter: int = 10
         p = r + (rho_new / rho) * p
         rho = rho_new
     return x, max_iter
+
+
+# ---------------------------------------------------------------------------
+# O3 over a batch of columns (large M): the same naive B-Lanczos as
+# lanczos_column, with the sparse products, the plain CG solves and the
+# pivoted tridiagonal solves in C (oracle/o3_batch.c, OpenMP). The columns of
+# a batch share only the traversal of the matrix; each column's arithmetic
+# is that of a one-column run, in the order of the steps above.
+# ---------------------------------------------------------------------------
+
+_O3 = None
+
+
+def _o3lib():
+    """Load (building on first use) the oracle's C loops."""
+    global _O3
+    if _O3 is None:
+        import ctypes
+
+        from . import build_c
+
+        lib = ctypes.CDLL(build_c.build())
+        P = ctypes.c_void_p
+        i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.o3_set_threads.argtypes = [i32]
+        lib.o3_get_threads.restype = i32
+        lib.o3_spmm.argtypes = [i64, P, P, P, i32, i32, P, P]
+        lib.o3_cg.argtypes = [i64, P, P, P, i32, i32, P, P, dbl, i32, P, P, P]
+        lib.o3_cg.restype = i32
+        lib.o3_seed.argtypes = [i64, P, P, P, i32, i32, P, dbl, i32] + [P] * 9
+        lib.o3_seed.restype = i32
+        lib.o3_step.argtypes = [i64, P, P, P, P, P, P, i32, i32, i32, dbl, i32] + [P] * 15
+        lib.o3_step.restype = i32
+        lib.o3_tridiag.argtypes = [i32, P, P, dbl, i32, P, P, P]
+        _O3 = lib
+    return _O3
+
+
+def set_threads(n: int) -> int:
+    """Threads of the C loops (0 keeps the current setting); returns the count in use."""
+    lib = _o3lib()
+    lib.o3_set_threads(int(n))
+    return int(lib.o3_get_threads())
+
+
+def _csr_parts(S):
+    ptr = np.ascontiguousarray(S.indptr, dtype=np.int64)
+    idx = np.ascontiguousarray(S.indices, dtype=np.int32)
+    val = np.ascontiguousarray(S.data, dtype=np.float64)
+    return ptr, idx, val
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data
+
+
+def tridiag_solve_c(alpha, beta, beta0, z, full: bool = False):
+    """(z_k I - T) y = beta0 e_1 for every shift z_k by the C pivoted elimination.
+
+    Returns y_n per shift, and y (S, n) when full."""
+    lib = _o3lib()
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    if b.size < max(a.size - 1, 1):
+        b = np.concatenate([b, np.zeros(max(a.size - 1, 1) - b.size)])
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+    last = np.zeros(zz.size, dtype=np.complex128)
+    y = np.zeros((zz.size, a.size), dtype=np.complex128) if full else None
+    lib.o3_tridiag(int(a.size), _p(a), _p(b), float(beta0), int(zz.size), _p(zz), _p(last),
+                   _p(y) if full else None)
+    return (last, y) if full else last
+
+
+def lanczos_batch(A, B, cols, z_per_col, tol: float = 1e-8, max_iter: int = 5000, check_every: int = 10,
+                  bsolve_tol: float = 1e-14, milestones=(), max_cg: int = 10000, progress=None,
+                  on_done=None):
+    """O3 for several columns at once; returns one LanczosResult per column.
+
+    z_per_col[c] holds the S shifts of column c (its own damping). Convergence
+    is tested, as in lanczos_column, every check_every steps (and at max_iter
+    or when u = 0): the residual of shift k is |y_n(z_k)| ||u_n||_2, and a
+    column stops when every shift is at or below tol. Finished columns leave
+    the batch, the others keep running; on_done(c, result) is called as each
+    column finishes.
+    """
+    lib = _o3lib()
+    cols = np.asarray(cols, dtype=np.int64)
+    C = int(cols.size)
+    M = int(A.shape[0])
+    ap, ai, av = _csr_parts(A)
+    bp, bi, bv = _csr_parts(B)
+    ld = C
+    st = {k: np.zeros((M, ld)) for k in ("q", "Bq", "Bqp", "u", "v", "R", "P", "BP")}
+    beta0 = np.zeros(ld)
+    beta_prev = np.zeros(ld)
+    alpha = np.zeros(ld)
+    beta = np.zeros(ld)
+    unorm = np.zeros(ld)
+    rows = [pattern_rows(A, int(j)) for j in cols]
+    zc = [np.asarray(z, dtype=np.complex128) for z in z_per_col]
+    active = list(range(C))
+    rows_act = np.ascontiguousarray(cols[active], dtype=np.int32)
+    cg = lib.o3_seed(M, _p(bp), _p(bi), _p(bv), C, ld, _p(rows_act), bsolve_tol, max_cg, _p(st["q"]),
+                     _p(st["Bq"]), _p(st["Bqp"]), _p(st["u"]), _p(st["v"]), _p(st["R"]), _p(st["P"]),
+                     _p(st["BP"]), _p(beta0))
+    if cg < 0:
+        raise RuntimeError("oracle CG did not converge on the seed")
+    b0 = {c: float(beta0[t]) for t, c in enumerate(active)}
+    alphas = {c: [] for c in range(C)}
+    betas = {c: [] for c in range(C)}
+    QP = {c: [] for c in range(C)}
+    out = [None] * C
+    reached = {c: {} for c in range(C)}
+    n = 0
+    while active:
+        n += 1
+        na = len(active)
+        off = np.zeros(na + 1, dtype=np.int64)
+        for t, c in enumerate(active):
+            off[t + 1] = off[t] + rows[c].size
+        prow = np.ascontiguousarray(np.concatenate([rows[c] for c in active]), dtype=np.int32)
+        qp = np.zeros(int(off[-1]))
+        cg = lib.o3_step(M, _p(ap), _p(ai), _p(av), _p(bp), _p(bi), _p(bv), na, ld, int(n == 1), bsolve_tol,
+                         max_cg, _p(st["q"]), _p(st["Bq"]), _p(st["Bqp"]), _p(st["u"]), _p(st["v"]),
+                         _p(st["R"]), _p(st["P"]), _p(st["BP"]), _p(beta_prev), _p(alpha), _p(beta),
+                         _p(unorm), _p(off), _p(prow), _p(qp))
+        if cg < 0:
+            raise RuntimeError(f"oracle CG did not converge at step {n}")
+        finished = []
+        for t, c in enumerate(active):
+            if n > 1:
+                betas[c].append(float(beta[t]))
+            alphas[c].append(float(alpha[t]))
+            QP[c].append(qp[off[t]:off[t + 1]].copy())
+            un = float(unorm[t])
+            if not (n % check_every == 0 or n == max_iter or un == 0.0):
+                continue
+            last = tridiag_solve_c(alphas[c], betas[c], b0[c], zc[c])
+            resid = np.abs(last) * un
+            for m in milestones:
+                if m not in reached[c] and resid.max() <= m:
+                    reached[c][m] = n
+            conv = bool(np.all(resid <= tol)) or un == 0.0
+            if conv or n == max_iter:
+                _, y = tridiag_solve_c(alphas[c], betas[c], b0[c], zc[c], full=True)
+                G = np.stack(QP[c], axis=1) @ y.T
+                r = LanczosResult(G, n, resid, conv, np.asarray(alphas[c]), np.asarray(betas[c]), b0[c])
+                r.reached = reached[c]
+                out[c] = r
+                QP[c] = None
+                if on_done is not None:
+                    on_done(c, r)
+                finished.append(t)
+        if finished:
+            keep = [t for t in range(na) if t not in finished]
+            for k in st:
+                st[k][:, :len(keep)] = st[k][:, keep]
+            for arr in (beta_prev,):
+                arr[:len(keep)] = arr[keep]
+            active = [active[t] for t in keep]
+        if progress is not None:
+            progress(n, len(active))
+    return out

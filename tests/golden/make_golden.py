@@ -1,12 +1,20 @@
 """Write oracle reference values for sampled columns of the large workloads.
 
-Calls only the CPU oracle (oracle/krylov.py, the naive FP64 B-Lanczos of
-Sec. III-B) and the seeded input generator. For each sampled column of a
+Calls only the CPU oracle (oracle/krylov.py: the naive FP64 B-Lanczos of
+Sec. III-B, one column at a time or a batch of columns through the oracle's
+C loops) and the seeded input generator. For each sampled column of a
 workload it stores: the column, its damping eta, the oracle's step count at
-the 1e-8 residual level, and G on the column's pattern at every shift_stride-th
-shift, from a run to a 1e-10 residual. Usage:
+the 1e-8 residual level, and G on the column's pattern at every
+shift_stride-th shift, from a run to a 1e-10 residual. Usage:
 
-    python tests/golden/make_golden.py ch20k 0 3      # workload, first, count
+    python tests/golden/make_golden.py ch20k 0 3            # workload, first, count (one column at a time)
+    python tests/golden/make_golden.py ch100k --batch 0.2:24 0.1:24
+        # a batch: the first 24 columns of the seeded subset with eta = 0.2
+        # and the first 24 with eta = 0.1 that have no stored file yet
+
+Columns are taken in the order of the workload's seeded column subset
+(synthetic.column_subset), each with its seeded damping
+(synthetic.eta_per_column).
 """
 
 import json
@@ -23,6 +31,12 @@ from oracle import krylov  # noqa: E402
 from paper_1609_08377_gb300 import synthetic as syn  # noqa: E402
 
 SHIFT_STRIDE = 8
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCE_ONE = ("oracle/krylov.py lanczos_column (naive FP64 B-Lanczos, CG inner solves to 1e-14), "
+              "tol 1e-10; Sec. III-B of arXiv:1609.08377 (generalized shifted equations)")
+SOURCE_BATCH = ("oracle/krylov.py lanczos_batch (naive FP64 B-Lanczos over a batch of columns, C loops in "
+                "oracle/o3_batch.c, CG inner solves to 1e-14), tol 1e-10; Sec. III-B of arXiv:1609.08377 "
+                "(generalized shifted equations)")
 
 
 def sample(name: str, seed: int = 0):
@@ -39,8 +53,22 @@ def sample(name: str, seed: int = 0):
     return wl, s, cols, eta, order
 
 
-def main():
-    name, first, count = sys.argv[1], int(sys.argv[2]), int(sys.argv[3])
+def _path(name, j):
+    return os.path.join(HERE, f"{name}_col{j}.json")
+
+
+def _record(name, wl, j, e, r, seconds, source):
+    return {
+        "source": source, "workload": name, "seed": 0, "column": int(j), "eta": float(e),
+        "n_shifts": int(wl.n_shifts), "shift_stride": SHIFT_STRIDE,
+        "iters_1e-8": int(r.reached.get(1e-8, -1)), "iters_1e-10": int(r.iters),
+        "converged": bool(r.converged), "seconds": seconds,
+        "G_re": [[float(v) for v in row] for row in r.G[:, ::SHIFT_STRIDE].real],
+        "G_im": [[float(v) for v in row] for row in r.G[:, ::SHIFT_STRIDE].imag],
+    }
+
+
+def one_by_one(name, first, count):
     wl, s, cols, eta, order = sample(name)
     eps = syn.energy_grid(wl.n_shifts)
     for t in order[first:first + count]:
@@ -48,19 +76,56 @@ def main():
         t0 = time.time()
         r = krylov.lanczos_column(s.A, s.B, j, syn.shifts(eps, e), tol=1e-10, max_iter=60000,
                                   milestones=(1e-8,))
-        out = {
-            "source": "oracle/krylov.py lanczos_column (naive FP64 B-Lanczos, CG inner solves to 1e-14), "
-                      "tol 1e-10; Sec. III-B of arXiv:1609.08377 (generalized shifted equations)",
-            "workload": name, "seed": 0, "column": j, "eta": e, "n_shifts": int(wl.n_shifts),
-            "shift_stride": SHIFT_STRIDE, "iters_1e-8": int(r.reached.get(1e-8, -1)),
-            "iters_1e-10": int(r.iters), "converged": bool(r.converged), "seconds": time.time() - t0,
-            "G_re": [[float(v) for v in row] for row in r.G[:, ::SHIFT_STRIDE].real],
-            "G_im": [[float(v) for v in row] for row in r.G[:, ::SHIFT_STRIDE].imag],
-        }
-        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_col{j}.json")
-        with open(path, "w") as f:
+        out = _record(name, wl, j, e, r, time.time() - t0, SOURCE_ONE)
+        with open(_path(name, j), "w") as f:
             json.dump(out, f)
         print(name, j, e, out["iters_1e-8"], out["iters_1e-10"], round(out["seconds"]), flush=True)
+
+
+def batch(name, classes):
+    """classes: list of (eta, count); one oracle batch over all chosen columns."""
+    wl = syn.WORKLOADS[name]
+    s = syn.make_system(wl.n_atoms, wl.c_fraction, 0)
+    n_cols = wl.n_cols if wl.n_cols is not None else s.M
+    cols = syn.column_subset(s.M, n_cols, 0)
+    eta = syn.eta_per_column(cols.size, 0) if wl.eta is None else np.full(cols.size, wl.eta)
+    pick = []
+    for e, k in classes:
+        got = 0
+        for t in np.nonzero(np.isclose(eta, e))[0].tolist():
+            if got == k:
+                break
+            if os.path.exists(_path(name, int(cols[t]))):
+                continue
+            pick.append(t)
+            got += 1
+    js = [int(cols[t]) for t in pick]
+    es = [float(eta[t]) for t in pick]
+    eps = syn.energy_grid(wl.n_shifts)
+    print(name, "batch of", len(js), "columns:", list(zip(js, es)), "threads", krylov.set_threads(0), flush=True)
+    t0 = time.time()
+
+    def progress(n, n_act):
+        if n % 500 == 0:
+            print(f"step {n}: {n_act} columns active, {time.time() - t0:.0f} s", flush=True)
+
+    def done(c, r):
+        out = _record(name, wl, js[c], es[c], r, time.time() - t0, SOURCE_BATCH)
+        with open(_path(name, js[c]), "w") as f:
+            json.dump(out, f)
+        print(name, js[c], es[c], out["iters_1e-8"], out["iters_1e-10"], round(out["seconds"]), flush=True)
+
+    krylov.lanczos_batch(s.A, s.B, js, [syn.shifts(eps, e) for e in es], tol=1e-10, max_iter=60000,
+                         milestones=(1e-8,), progress=progress, on_done=done)
+
+
+def main():
+    name = sys.argv[1]
+    if sys.argv[2] == "--batch":
+        classes = [(float(a), int(b)) for a, b in (x.split(":") for x in sys.argv[3:])]
+        batch(name, classes)
+    else:
+        one_by_one(name, int(sys.argv[2]), int(sys.argv[3]))
 
 
 if __name__ == "__main__":
