@@ -1,23 +1,38 @@
 """Throughput benchmark of the generalized shifted Green's-function solver.
 
 Metric: column.shift solves per second at a 1e-8 relative residual for every
-shift, on a seeded synthetic C/H pencil. One step = one gsk_solve over a batch
-of columns (every row of the hot path: seed, A-SpMM, three-term update,
-inner B-solve, per-shift recurrences, convergence, work-queue refill).
+shift (Sec. III-A, the generalized shifted equations (z_k B - A) x = e_j),
+on a seeded synthetic C/H pencil. One step = one gsk_solve over a batch of
+columns: every row of the hot path (seed, A-SpMM, three-term update, inner
+B-solve, per-shift recurrences, convergence, work-queue refill).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ch20k] [--cols-per-step C] [--precision mixed|fp64]
+                  [--workload ch100k] [--cols-per-step C] [--precision mixed_df|mixed|fp64]
 
-Under torchrun (N > 1) every rank solves its own column batches (the columns
-are independent: weak scaling, no collective on the data path); the step time
-is the maximum over ranks. --impl reference times the CPU oracle (a naive
-FP64 B-Lanczos) on the host cores on a bounded sample of the same workload.
+Default workload: the 100,000-atom C/H pencil (M = 199,999), 128 shifts,
+16,384 seeded columns with damping drawn per column from {0.05, 0.1, 0.2} eV,
+double-float mixed precision with the learned scheduler. The learned model
+orders the whole column set longest-predicted-first; a batch is C consecutive
+columns of that order, and the warm-up and timed batches are evenly spaced
+over it (a stratified sample of the set, assigned to ranks round-robin), so
+the timed steps cover the set's mix of short and long columns. Seeded
+columns with stored oracle references (tests/golden) take the place of
+columns of the same damping in the timed batches; their error against the
+oracle is reported in the line.
+
+Under torchrun (N > 1) every rank solves its own batches (columns are
+independent: weak scaling, no collective on the data path); the step time is
+the maximum over ranks, and the per-shift traces of the last batch are summed
+over ranks once (the method's one collective) to report the chemical
+potential. --impl reference times the CPU oracle (the naive FP64 B-Lanczos,
+oracle/krylov.py) on the host cores on a bounded sample of the same workload.
 Prints one JSON line (rank 0).
 """
 
 from __future__ import annotations
 
 import argparse
+import glob
 import json
 import os
 import subprocess
@@ -30,31 +45,30 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1609_08377_gb300.profile_spmm import atom_blocks, spmm_alg_bytes  # noqa: E402
-
 METRIC = "column·shift solves/s at 1e-8 resid"
 UNIT = "column-shift solves/s"
+MU, KT = -10.0, 0.1          # Fermi function of the density checks (Eq. EQ-FD-FUNC)
 
 
 def _parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ch20k")
-    ap.add_argument("--cols-per-step", type=int, default=128)
+    ap.add_argument("--workload", default="ch100k")
+    ap.add_argument("--cols-per-step", type=int, default=32)
     ap.add_argument("--precision", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
     ap.add_argument("--batch-w", type=int, default=0)
     ap.add_argument("--sched", default="learned", choices=["fifo", "learned"])
     ap.add_argument("--no-graph", action="store_true", help="host-driven loop (for kernel-level profiling)")
-    ap.add_argument("--no-marnoldi", action="store_true", help="skip the multiple Arnoldi measurement")
+    ap.add_argument("--no-extras", action="store_true", help="only the headline (no FP64, e2e, Arnoldi, CPU legs)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------
-# workload
+# workload and batches
 # ---------------------------------------------------------------------------
 def make_workload(name: str, seed: int):
     from paper_1609_08377_gb300 import synthetic as syn
@@ -64,37 +78,86 @@ def make_workload(name: str, seed: int):
     eps = syn.energy_grid(wl.n_shifts)
     n_cols = wl.n_cols if wl.n_cols is not None else sys_.M
     cols = syn.column_subset(sys_.M, n_cols, seed)
-    # shuffle the subset (seeded) so consecutive batches mix the damping classes
-    rng = np.random.default_rng(seed + 31)
-    cols = cols[rng.permutation(cols.size)]
-    if wl.eta is None:
-        eta = syn.eta_per_column(cols.size, seed)
-    else:
-        eta = np.full(cols.size, wl.eta)
+    eta = syn.eta_per_column(cols.size, seed) if wl.eta is None else np.full(cols.size, wl.eta)
     return wl, sys_, eps, cols, eta
 
 
 def workload_config(wl, sys_, S: int, C: int, args, world: int) -> dict:
     """The workload description shared by both arms of the benchmark."""
     return {"workload": f"{wl.name}: {sys_.n_atoms} atoms (1/3 C 4-orbital, 2/3 H 1-orbital), "
-                        f"M={sys_.M}, nnz={sys_.nnz}, {S} shifts on [-25,5] eV, eta per column in "
-                        f"{{0.05,0.1,0.2}} eV, {C} seeded columns per step",
+                        f"M={sys_.M}, nnz={sys_.nnz}, {S} shifts on [-25,5] eV, {wl.n_cols or sys_.M} seeded "
+                        f"columns with eta per column in {{0.05,0.1,0.2}} eV; {C} columns per step, "
+                        f"consecutive in the learned longest-first order of the set, steps evenly spaced "
+                        f"over that order",
             "cols_per_step": C, "n_shifts": S, "tol": 1e-8, "precision": args.precision,
-            "sched": args.sched, "graph": not args.no_graph, "l2": "flushed between steps (256 MB write)",
+            "sched": args.sched, "graph": not args.no_graph,
+            "l2": "inputs larger than L2 (the pencil and lane vectors exceed 129 MB) and L2 flushed between "
+                  "steps (256 MB write)",
             "parallelism": f"columns sharded over {world} rank(s)"}
 
 
-def rank_batches(n_cols: int, C: int, n_batches: int, rank: int, world: int):
-    """Column ranges [a, b) of this rank's batches: batch b of rank r is block
-    (b * world + r) of C consecutive columns of the (shuffled) column set, so
-    ranks never share a column within a run (weak scaling: every rank solves
-    n_batches blocks of C columns)."""
-    n_blocks = max(1, n_cols // C)
+def learned_order(solver, cols, eta, args):
+    """Columns longest-predicted-first (the learned scheduler's order), or as
+    given for FIFO."""
+    if args.sched != "learned":
+        return np.arange(cols.size)
+    import torch
+
+    from paper_1609_08377_gb300 import gsk, scheduler
+
+    feat = torch.empty((cols.size, gsk.MLP_IN), dtype=torch.float32, device="cuda")
+    solver.features(cols, eta, feat)
+    pred = scheduler.predict(scheduler.load(), feat.cpu().numpy())
+    return np.argsort(-pred, kind="stable")
+
+
+def goldens(name: str):
     out = []
-    for b in range(n_batches):
-        k = (b * world + rank) % n_blocks
-        out.append((k * C, min(n_cols, (k + 1) * C)))
+    for p in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", f"{name}_col*.json"))):
+        out.append(json.load(open(p)))
     return out
+
+
+def place_goldens(batches, timed, refs, per_batch: int = 4):
+    """Put stored-reference columns into the timed batches, each into a batch
+    whose columns mostly share its damping, in place of a column of that
+    damping (at most per_batch per batch). Returns {batch: [ref, ...]}."""
+    placed = {}
+    for r in refs:
+        j, e = int(r["column"]), float(r["eta"])
+        for b in timed:
+            c, et = batches[b]
+            if len(placed.get(b, [])) >= per_batch or j in c:
+                continue
+            same = np.nonzero(np.isclose(et, e))[0]
+            if same.size * 2 < et.size:
+                continue
+            used = {int(np.nonzero(c == int(x["column"]))[0][0]) for x in placed.get(b, [])}
+            slot = next((int(t) for t in same[::-1] if int(t) not in used), None)
+            if slot is None:
+                continue
+            c = c.copy()
+            c[slot] = j
+            batches[b] = (c, et)
+            placed.setdefault(b, []).append(r)
+            break
+    return placed
+
+
+def atom_blocks(s) -> int:
+    """(atom, neighbour atom) pairs of the pattern: the neighbour index entries
+    of the block layout before padding."""
+    atom = s.atom_of_row()
+    coo = s.A.tocoo()
+    return int(np.unique(atom[coo.row].astype(np.int64) * s.n_atoms + atom[coo.col]).size)
+
+
+def spmm_alg_bytes(s, n_blocks: int, W: int, bv: int = 4) -> int:
+    """Algorithmic bytes of one inner-CG product on W lanes of bv-byte values:
+    the stored values once, one neighbour index per atom block, the atom
+    pointers, X read once, and the direction P and the product Y each read
+    and written once."""
+    return s.nnz * bv + n_blocks * 4 + (s.n_atoms + 1) * 4 + 5 * s.M * W * bv
 
 
 def max_over_ranks(t_local: float, dist=None, device=None) -> float:
@@ -168,32 +231,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample)
-# ---------------------------------------------------------------------------
-def oracle_rate(sys_, eps, cols, eta, mean_iters: float, budget_s: float = 15.0) -> dict:
-    """Time the oracle's naive B-Lanczos (as it stands) for a bounded number of
-    steps of one column and scale by the solver's mean iteration count."""
-    from oracle import krylov
-    from paper_1609_08377_gb300 import synthetic as syn
-
-    j = int(cols[0])
-    z = syn.shifts(eps, float(eta[0]))
-    # probe the cost of a step, then run as many as fit the budget
-    t0 = time.perf_counter()
-    krylov.lanczos_column(sys_.A, sys_.B, j, z, tol=1e-30, max_iter=2, check_every=10 ** 9)
-    t_probe = (time.perf_counter() - t0) / 3.0          # seed + 2 steps ~ 3 B-solves
-    n = int(max(3, min(400, budget_s / max(t_probe, 1e-6))))
-    t0 = time.perf_counter()
-    krylov.lanczos_column(sys_.A, sys_.B, j, z, tol=1e-30, max_iter=n, check_every=10 ** 9)
-    dt = time.perf_counter() - t0
-    per_step = dt / (n + 1)
-    per_col = per_step * max(mean_iters, 1.0)
-    rate = len(eps) / per_col
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle B-Lanczos (FP64, NumPy/SciPy, single-threaded sparse products) on column {j}: "
-                      f"{n} Lanczos steps in {dt:.1f} s, scaled by the GPU solver's mean {mean_iters:.0f} "
-                      f"steps per column and {len(eps)} shifts per column"}
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
 # ---------------------------------------------------------------------------
@@ -220,18 +264,24 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
 
-    from paper_1609_08377_gb300 import gsk
+    from paper_1609_08377_gb300 import gsk, scheduler, sharding
 
     wl, sys_, eps, cols_all, eta_all = make_workload(args.workload, args.seed)
     S = eps.size
     z = eps.astype(np.complex128) + 1j * 1.0        # real parts; damping per column via eta
     solver = gsk.from_system(sys_)
     if args.sched == "learned":
-        from paper_1609_08377_gb300 import scheduler
         scheduler.install(solver, scheduler.load())
     C = args.cols_per_step
-    n_batches = args.warmup + args.steps + 1
-    batches = [(cols_all[a:b], eta_all[a:b]) for a, b in rank_batches(cols_all.size, C, n_batches, rank, world)]
+    order = learned_order(solver, cols_all, eta_all, args)
+    n_chunks = cols_all.size // C
+    n_batches = args.warmup + args.steps
+    chunks = sharding.stratified_batches(n_chunks, n_batches, rank, world, args.seed)
+    batches = [(cols_all[order[k * C:(k + 1) * C]].copy(), eta_all[order[k * C:(k + 1) * C]].copy())
+               for k in chunks]
+    timed = list(range(args.warmup, n_batches))
+    refs = goldens(wl.name)
+    placed = place_goldens(batches, timed, refs) if refs else {}
     max_elem = max(int(solver.pattern_offsets(c)[-1]) for c, _ in batches)
     G = torch.empty(max_elem * S, dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -239,26 +289,24 @@ def main():
     opts = dict(precision=args.precision, tol=1e-8, batch_w=args.batch_w,
                 sched=args.sched, use_graph=0 if args.no_graph else 1, stream=stream.cuda_stream)
 
-    def step(b, Gbuf):
-        c, e = batches[b]
-        return solver.solve(z, c, Gbuf, eta=e, **opts)
-
-    # lane width: autotuned on the first batch (setup, untimed) unless given
-    tuned_w = args.batch_w
+    # lane width and inner-CG kernel: autotuned on the first batch (setup, untimed) unless given
+    tuned = {}
     if args.batch_w == 0:
-        tuned_w = solver.autotune(z, batches[0][0], eta=batches[0][1], precision=args.precision,
-                                  stream=stream.cuda_stream)
+        solver.autotune(z, batches[0][0], eta=batches[0][1], precision=args.precision, stream=stream.cuda_stream)
+        tuned = solver.autotune_result(args.precision)
 
     for b in range(args.warmup):
         flush.zero_()
-        step(b, G)
+        solver.solve(z, batches[b][0], G, eta=batches[b][1], **opts)
     torch.cuda.synchronize(dev)
 
     clocks = ClockSampler(local_rank)
     clocks.start()
     times, launches, iters_all, status_all, outer = [], 0, [], [], 0
-    for i in range(args.steps):
-        b = args.warmup + i
+    gerr, rerr, n_checked = 0.0, 0.0, 0
+    last_stats = {}
+    for b in timed:
+        c, e = batches[b]
         flush.zero_()
         if dist is not None:
             dist.barrier()
@@ -266,16 +314,18 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        it, st, rs = step(b, G)
+        it, st, rs = solver.solve(z, c, G, eta=e, **opts)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        times.append(ms)
-        stt = solver.last_stats()
-        launches += int(stt["kernel_launches"])
-        outer += int(stt["outer_steps"])
+        times.append(e0.elapsed_time(e1))
+        last_stats = solver.last_stats()
+        launches += int(last_stats["kernel_launches"])
+        outer += int(last_stats["outer_steps"])
         iters_all.append(it)
         status_all.append(st)
+        if b in placed:                     # untimed: the stored oracle columns of this batch
+            ge, re_ = oracle_errors(solver, c, G, placed[b], eps, S, dev)
+            gerr, rerr, n_checked = max(gerr, ge), max(rerr, re_), n_checked + len(placed[b])
     clock = clocks.stop()
     t_local = float(np.sum(times))
     t_total = max_over_ranks(t_local, dist, dev)
@@ -283,44 +333,9 @@ def main():
     value = solves / (t_total / 1e3)
     iters_all = np.concatenate(iters_all)
     status_all = np.concatenate(status_all)
-
-    # ---- end to end through the C ABI with host buffers ----
-    b = args.warmup + args.steps
-    c_e2e, eta_e2e = batches[b]
-    n_elem = int(solver.pattern_offsets(c_e2e)[-1])
-    G_host = torch.empty(n_elem * S, dtype=torch.complex128).pin_memory()
-    cols_h = torch.from_numpy(np.ascontiguousarray(c_e2e, dtype=np.int32)).pin_memory()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    solver.solve(z, cols_h.numpy(), G_host, eta=eta_e2e, **opts)
-    torch.cuda.synchronize(dev)
-    t_e2e = time.perf_counter() - t0
-    h2d = (n_elem * 4 + C * (8 + 4 + 4 + 4 + 8) + 8 + 16 * S)
-    d2h = n_elem * S * 16 + C * (4 + 4 + 8)
-    e2e = {"value": C * S / t_e2e * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "steps": 1}
-
-    # ---- roofline of the dominant kernel: the block SpMM ----
-    roof = spmm_roofline(solver, sys_, args, stream, dev)
-
-    # ---- against the plain FP64 solver: time per lock-step Lanczos step on the
-    # same columns and lane width (both precisions converge in the same number
-    # of steps to within a few per cent, so the per-step ratio is the speed-up)
-    vs_fp64 = None
-    if args.precision != "fp64":
-        try:
-            vs_fp64 = vs_plain_fp64(solver, batches, args, z, G, tuned_w, stream, dev)
-        except Exception as exc:
-            vs_fp64 = {"error": f"{type(exc).__name__}: {exc}"}
-
-    # ---- the paper's own approximation on the same pencil: multiple Arnoldi,
-    # nu = 30, analytic Fermi integration (rho on every column's pattern) ----
-    marn = None
-    if rank == 0 and not args.no_marnoldi:
-        try:
-            marn = marnoldi_rate(solver, sys_, dev)
-        except Exception as exc:        # an extra measurement must not cost the headline line
-            marn = {"error": f"{type(exc).__name__}: {exc}"}
+    W_used = int(last_stats.get("batch_w", 0))
+    kern = {gsk.GSK_SPMM_GATHER: "gather", gsk.GSK_SPMM_STAGED: "staged"}.get(
+        int(last_stats.get("spmm_kernel", 0)), "?")
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -329,58 +344,204 @@ def main():
         "dtype": {"mixed_df": "f32+f32x2+f64", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded C/H tight-binding-like pencil standing in for the paper's PPE structures)",
         "config": workload_config(wl, sys_, S, C, args, world),
-        "batch_w": int(solver.last_stats()["batch_w"]), "batch_w_autotuned": args.batch_w == 0,
-        "roofline": roof,
-        "vs_plain_fp64": vs_fp64,
-        "marnoldi": marn,
-        "e2e": e2e,
+        "batch_w": W_used, "spmm_kernel": kern, "autotuned": tuned or None,
+        "oracle_error": {"dG_rel_max": gerr if n_checked else None, "drho_rel_max": rerr if n_checked else None,
+                         "columns": n_checked,
+                         "how": "stored oracle columns (tests/golden: naive FP64 B-Lanczos to 1e-10) solved "
+                                "inside the timed batches; |dG|/max|G| over their pattern at every 8th shift, "
+                                "and rho from those 16 shifts (trapezoid) against the oracle's rho from the "
+                                "same 16 shifts"},
         "gpu_launches": launches,
         "clocks": clock,
         "solver": {"mean_iters": float(iters_all.mean()), "max_iters": int(iters_all.max()),
                    "converged": int((status_all == 0).sum()), "columns": int(status_all.size),
                    "outer_steps": outer},
     }
-    if rank == 0:
+    extras = not args.no_extras
+
+    # ---- end to end through the C ABI with host buffers, over timed batches ----
+    out["e2e"] = e2e_rate(solver, batches, timed, times, z, S, opts, dev, world) if extras else None
+
+    # ---- the method's one collective: per-shift traces summed over ranks, mu ----
+    try:
+        out["mu"] = global_mu(solver, batches[timed[-1]], G, eps, S, dist, dev)
+    except Exception as exc:
+        out["mu"] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # ---- roofline of the dominant kernel: the inner-CG B-product ----
+    out["roofline"] = spmm_roofline(solver, sys_, W_used or 32, kern, args, stream, dev)
+
+    if extras:
+        # plain FP64 on the same columns, both solved to 1e-8
         try:
-            out["cpu_baseline"] = oracle_rate(sys_, eps, cols_all, eta_all, float(iters_all.mean()))
+            out["vs_plain_fp64"] = vs_plain_fp64(solver, cols_all, eta_all, order, C, z, S, G, args, stream, dev)
         except Exception as exc:
-            out["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}", "kind": "oracle"}
+            out["vs_plain_fp64"] = {"error": f"{type(exc).__name__}: {exc}"}
+        if rank == 0:
+            try:
+                out["marnoldi"] = marnoldi_rate(solver, sys_, dev)
+            except Exception as exc:
+                out["marnoldi"] = {"error": f"{type(exc).__name__}: {exc}"}
+            try:
+                out["cpu_baseline"] = oracle_rate(sys_, eps, cols_all, eta_all, float(iters_all.mean()))
+            except Exception as exc:
+                out["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}", "kind": "oracle"}
+    if rank == 0:
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
 
-def vs_plain_fp64(solver, batches, args, z, G, tuned_w, stream, dev) -> dict:
-    """Time per lock-step Lanczos step of the production precision and of plain
-    FP64 on the same columns and lane width (both converge in the same number
-    of steps to within a few per cent, so the per-step ratio is the speed-up)."""
+def oracle_errors(solver, c, G, refs, eps, S, dev):
+    """|dG|/max|G| and the rho error of the stored oracle columns in batch c."""
     import torch
 
-    c_cmp, e_cmp = batches[args.warmup]
-    per = {}
+    from oracle import density
+    from paper_1609_08377_gb300 import synthetic as syn
+
+    off = solver.pattern_offsets(c)
+    Gh = G[: int(off[-1]) * S].view(int(off[-1]), S)
+    stride = int(refs[0]["shift_stride"])
+    eps_s = eps[::stride]
+    w_s = syn.trapezoid_weights(eps_s)
+    gerr = rerr = 0.0
+    for r in refs:
+        t = int(np.nonzero(c == int(r["column"]))[0][0])
+        got = Gh[int(off[t]):int(off[t + 1]), ::stride].contiguous()
+        R = np.array(r["G_re"]) + 1j * np.array(r["G_im"])
+        g = got.cpu().numpy()
+        gerr = max(gerr, float(np.abs(g - R).max() / np.abs(R).max()))
+        rho = torch.empty(got.shape[0], dtype=torch.float64, device=dev)
+        solver.density(got.reshape(-1), eps_s, w_s, MU, KT, rho, got.shape[0])
+        torch.cuda.synchronize(dev)
+        ro = density.density_from_green(R, eps_s, w_s, MU, KT)
+        rerr = max(rerr, float(np.abs(rho.cpu().numpy() - ro).max() / np.abs(ro).max()))
+    return gerr, rerr
+
+
+def e2e_rate(solver, batches, timed, times, z, S, opts, dev, world, n: int = 4) -> dict:
+    """The same metric through the C ABI with host buffers: inputs from the
+    host and G into pinned host memory, wall clock around each call, on n of
+    the timed batches (evenly spaced); the device-timed rate of the same
+    batches is given beside it."""
+    import torch
+
+    pick = [timed[int(i)] for i in np.linspace(0, len(timed) - 1, min(n, len(timed))).round().astype(int)]
+    pick = sorted(set(pick))
+    t_wall, t_dev, h2d, d2h = 0.0, 0.0, 0, 0
+    for b in pick:
+        c, e = batches[b]
+        n_elem = int(solver.pattern_offsets(c)[-1])
+        G_host = torch.empty(n_elem * S, dtype=torch.complex128).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        solver.solve(z, np.ascontiguousarray(c, dtype=np.int32), G_host, eta=np.ascontiguousarray(e), **opts)
+        torch.cuda.synchronize(dev)
+        t_wall += time.perf_counter() - t0
+        t_dev += times[timed.index(b)] / 1e3
+        h2d = max(h2d, n_elem * 4 + c.size * (8 + 4 + 4 + 4 + 8) + 8 + 16 * S)
+        d2h = max(d2h, n_elem * S * 16 + c.size * (4 + 4 + 8))
+    C = batches[pick[0]][0].size
+    return {"value": len(pick) * C * S / t_wall * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": len(pick),
+            "device_timed_same_batches": len(pick) * C * S / t_dev * world,
+            "how": f"{len(pick)} of the timed batches re-run through gsk_solve with host buffers (pinned G), "
+                   "wall clock per call"}
+
+
+def global_mu(solver, batch, G, eps, S, dist, dev) -> dict:
+    """Per-shift traces s_k = sum Im G B of a batch, summed over ranks (the
+    paper's all-reduce of trace quantities, Sec. III-C), and the chemical
+    potential for the batch's own electron count at kT = 0.1."""
+    from paper_1609_08377_gb300 import sharding
+    from paper_1609_08377_gb300 import synthetic as syn
+
+    c, _ = batch
+    w = syn.trapezoid_weights(eps)
+    s = sharding.global_shift_traces(lambda cc: solver.shift_trace(cc, S, G, 1), c, dist, dev)
+    n_elec = float(-(1.0 / np.pi) * np.sum(w * s * (eps <= MU)))      # electrons below MU at kT -> 0
+    mu, count = solver.mu_from_traces(eps, w, s, KT, n_elec, -30.0, 10.0)
+    return {"mu": mu, "count": count, "n_elec": n_elec, "ranks": dist.get_world_size() if dist else 1,
+            "how": "per-shift traces of the last timed batch all-reduced over ranks, mu from gsk_mu_from_traces"}
+
+
+def vs_plain_fp64(solver, cols_all, eta_all, order, C, z, S, G, args, stream, dev) -> dict:
+    """The production precision and plain FP64 on the same columns, both to
+    a 1e-8 residual: the C shortest-predicted columns of the set (the FP64
+    solve of a long batch would take minutes), same lane width."""
+    import torch
+
+    sel = order[-C:]
+    c, e = cols_all[sel], eta_all[sel]
+    Gc = torch.empty(int(solver.pattern_offsets(c)[-1]) * S, dtype=torch.complex128, device=dev)
+    out = {}
     for prec in (args.precision, "fp64"):
-        for _ in range(2):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            solver.solve(z, c_cmp, G, eta=e_cmp, precision=prec, tol=1e-8, max_iter=60,
-                         batch_w=tuned_w, sched="fifo", stream=stream.cuda_stream)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-        per[prec] = e0.elapsed_time(e1) / solver.last_stats()["outer_steps"]
-    return {"ratio": per["fp64"] / per[args.precision], "ms_per_step": per,
-            "how": f"60 lock-step Lanczos steps of the same {c_cmp.size} columns at W={tuned_w}, "
-                   "CUDA events; iteration counts of the two precisions agree to a few per cent"}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st, _ = solver.solve(z, c, Gc, eta=e, precision=prec, tol=1e-8, batch_w=32, sched=args.sched,
+                                 stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = e0.elapsed_time(e1) / 1e3
+        out[prec] = {"value": C * S / sec, "unit": UNIT, "seconds": sec, "mean_iters": float(it.mean()),
+                     "converged": int((st == 0).sum())}
+    return {"ratio": out[args.precision]["value"] / out["fp64"]["value"], "by_precision": out,
+            "how": f"{C} columns (the shortest-predicted of the set) solved to 1e-8 in each precision at W=32, "
+                   "CUDA events around gsk_solve"}
 
 
-FP64_TFLOPS = 1.20     # measured FP64 FMA throughput of this GPU (FMA microbenchmark)
+def spmm_roofline(solver, sys_, W, kern, args, stream, dev) -> dict:
+    """CUDA-event timing of the solve's inner-CG B-product kernel (the same
+    kernel and launch shape, through gsk_spmm) and its algorithmic HBM bytes
+    per launch. The pencil and lane vectors exceed L2, so back-to-back
+    launches read from HBM."""
+    import torch
+
+    from paper_1609_08377_gb300 import gsk
+
+    prec = gsk.GSK_FP64 if args.precision == "fp64" else gsk.GSK_MIXED
+    dt = torch.float32 if prec == gsk.GSK_MIXED else torch.float64
+    which = 2 if (kern == "staged" and prec == gsk.GSK_MIXED) else 1
+    M = sys_.M
+    X = torch.randn(M * W, dtype=dt, device=dev)
+    Y = torch.empty(M * W, dtype=dt, device=dev)
+    solver.spmm(which, prec, W, X, Y, n_rep=3, stream=stream)
+    torch.cuda.synchronize(dev)
+    reps = 30
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.spmm(which, prec, W, X, Y, n_rep=reps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    bv = 4 if prec == gsk.GSK_MIXED else 8
+    alg = spmm_alg_bytes(sys_, atom_blocks(sys_), W, bv)
+    peaks = _peaks()
+    achieved = alg / sec / 1e9
+    cap = _NCU_TRAFFIC.get((args.workload, kern, bv, W))
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": cap[0] if cap else None,
+            "traffic_source": cap[1] if cap else "no ncu capture of this kernel and shape",
+            "kernel": f"inner-CG B product ({kern}, {'FP32' if bv == 4 else 'FP64'}, W={W}) x{reps} via gsk_spmm",
+            "ms_per_launch": sec * 1e3, "alg_bytes_per_launch": int(alg), "peak_source": peaks["source"]}
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# inner-CG product from one ncu capture per (workload, kernel, value bytes, W),
+# with the profiles/ summary that records it
+_NCU_TRAFFIC = {
+    ("ch100k", "staged", 4, 32): (None, ""),
+}
+_NCU_TRAFFIC = {k: v for k, v in _NCU_TRAFFIC.items() if v[0] is not None}
 
 
 def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
     """Columns per second of gsk_marnoldi (rho on the pattern, nu = 30) on a
     seeded column subset, its dominant kernel (the FP64 A-product of the
-    64-lane Lanczos) against the FP64 ALU rate, and the oracle's rate on one
-    host core for two columns."""
+    64-lane Lanczos) against the FP64 FMA rate measured now (gsk_alu_peak),
+    and the oracle's rate on one host core for two columns."""
     import torch
 
     from oracle import marnoldi as ma
@@ -389,7 +550,7 @@ def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
     cols = syn.column_subset(sys_.M, n_cols, 7)
     off = solver.pattern_offsets(cols)
     rho = torch.empty(int(off[-1]), dtype=torch.float64, device=dev)
-    solver.marnoldi(cols[:32], nu, -10.0, 0.1, rho)
+    solver.marnoldi(cols[:32], nu, MU, KT, rho)
     torch.cuda.synchronize(dev)
     ds = torch.cuda.default_stream(dev)
     best = None
@@ -397,7 +558,7 @@ def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(ds)
-        _, _, charge, rank = solver.marnoldi(cols, nu, -10.0, 0.1, rho)
+        _, _, charge, rank = solver.marnoldi(cols, nu, MU, KT, rho)
         e1.record(ds)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
@@ -416,11 +577,16 @@ def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
     torch.cuda.synchronize(dev)
     sec = e0.elapsed_time(e1) / 1e3 / 20
     flops = 2.0 * sys_.nnz * W
+    # the FP64 and FP32 FMA rates of this GPU, measured now with clocks sampled
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    p64 = gsk.alu_peak(gsk.GSK_FP64, 5)
+    p32 = gsk.alu_peak(gsk.GSK_MIXED, 5)
+    clk_rec = clk.stop()
     t0 = time.perf_counter()
     for j in cols[:2]:
-        ma.marnoldi_column(sys_.A, sys_.B, int(j), nu, mu=-10.0, kT=0.1)
+        ma.marnoldi_column(sys_.A, sys_.B, int(j), nu, mu=MU, kT=KT)
     cpu = 2 / (time.perf_counter() - t0)
-    # the same with the paper's real-space projection (kappa = 100 atoms)
     proj = None
     try:
         proj = projected_rate(solver, sys_, cols, nu, dev)
@@ -429,11 +595,12 @@ def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
     return {"value": n_cols / (best / 1e3), "unit": "columns/s", "nu": nu, "columns": n_cols,
             "charge_sum_max_err": float(np.abs(charge.sum(axis=1) - 1.0).max()),
             "rank_min": int(rank.min()),
-            "roofline": {"bound": "alu", "achieved": flops / sec / 1e12, "peak": FP64_TFLOPS,
-                         "unit": "TFLOP/s", "frac": flops / sec / 1e12 / FP64_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": flops / sec / 1e12, "peak": p64,
+                         "unit": "TFLOP/s", "frac": flops / sec / 1e12 / p64, "traffic": None,
                          "kernel": "k_spmm<double> A-product, W=64 (FP64 FMAs: 2 nnz W per launch)",
                          "ms_per_launch": sec * 1e3,
-                         "peak_source": "measured FP64 FMA throughput (microbenchmark)"},
+                         "peak_source": "gsk_alu_peak: FP64 FMA chains measured in this run",
+                         "fp32_tflops": p32, "clocks": clk_rec},
             "cpu_baseline": {"value": cpu, "unit": "columns/s", "cores": 1, "kind": "oracle",
                              "sample": "oracle multiple Arnoldi (NumPy/SciPy) on 2 of the columns"},
             "projected": proj}
@@ -445,122 +612,103 @@ def projected_rate(solver, sys_, cols, nu, dev):
     assembly included)."""
     import torch
 
-    proj = None
-    if getattr(sys_, "box", None) is not None:
-        box = (float(sys_.box),) * 3 if np.isscalar(sys_.box) else tuple(float(b) for b in sys_.box)
-        pc = cols[:128]
-        poff = solver.pattern_offsets(pc)
-        prho = torch.empty(int(poff[-1]), dtype=torch.float64, device=dev)
-        solver.marnoldi_projected(pc[:32], 100, nu, -10.0, 0.1, prho, box=box)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        _, _, pq, prank, m_loc = solver.marnoldi_projected(pc, 100, nu, -10.0, 0.1, prho, box=box)
-        torch.cuda.synchronize(dev)
-        tp = time.perf_counter() - t0
-        proj = {"value": pc.size / tp, "unit": "columns/s", "kappa": 100, "columns": int(pc.size),
-                "m_local_mean": float(np.mean(m_loc)), "charge_sum_max_err": float(np.abs(pq.sum(axis=1) - 1.0).max()),
-                "how": "wall time of the synchronous call, host region search and pencil assembly included"}
-    return proj
-
-
-def spmm_roofline(solver, sys_, args, stream, dev) -> dict:
-    """CUDA-event timing of the solver's FP32 B-SpMM kernel (the inner-solve
-    product) through gsk_spmm, and its algorithmic HBM bytes per launch."""
-    import torch
-
-    from paper_1609_08377_gb300 import gsk
-
-    W = int(solver.last_stats()["batch_w"]) or 64
-    prec = gsk.GSK_FP64 if args.precision == "fp64" else gsk.GSK_MIXED
-    dt = torch.float32 if prec == gsk.GSK_MIXED else torch.float64
-    M = sys_.M
-    X = torch.randn(M * W, dtype=dt, device=dev)
-    Y = torch.empty(M * W, dtype=dt, device=dev)
-    solver.spmm(1, prec, W, X, Y, n_rep=3, stream=stream)
+    box = (float(sys_.box),) * 3 if np.isscalar(sys_.box) else tuple(float(b) for b in sys_.box)
+    pc = cols[:128]
+    poff = solver.pattern_offsets(pc)
+    prho = torch.empty(int(poff[-1]), dtype=torch.float64, device=dev)
+    solver.marnoldi_projected(pc[:32], 100, nu, MU, KT, prho, box=box)
     torch.cuda.synchronize(dev)
-    reps = 50
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    solver.spmm(1, prec, W, X, Y, n_rep=reps, stream=stream)
-    e1.record(stream)
+    t0 = time.perf_counter()
+    _, _, pq, prank, m_loc = solver.marnoldi_projected(pc, 100, nu, MU, KT, prho, box=box)
     torch.cuda.synchronize(dev)
-    sec = e0.elapsed_time(e1) / 1e3 / reps
-    bv = 4 if prec == gsk.GSK_MIXED else 8
-    alg = spmm_alg_bytes(sys_, atom_blocks(sys_), W, bv)
-    peaks = _peaks()
-    achieved = alg / sec / 1e9
-    # DRAM bytes (read + write) per launch from one ncu capture of this shape; None otherwise
-    traffic = _NCU_TRAFFIC.get((args.workload, bv, W))
-    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": f"k_spmm (inner-CG B product, {'FP32' if bv == 4 else 'FP64'}, W={W}) x{reps} via gsk_spmm",
-            "ms_per_launch": sec * 1e3, "alg_bytes_per_launch": int(alg),
-            "peak_source": peaks["source"]}
+    tp = time.perf_counter() - t0
+    return {"value": pc.size / tp, "unit": "columns/s", "kappa": 100, "columns": int(pc.size),
+            "m_local_mean": float(np.mean(m_loc)), "charge_sum_max_err": float(np.abs(pq.sum(axis=1) - 1.0).max()),
+            "how": "wall time of the synchronous call, host region search and pencil assembly included"}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# FP32 CG product, one ncu capture per (workload, value bytes, W)
-_NCU_TRAFFIC = {("ch20k", 4, 64): 52.84e6, ("ch100k", 4, 64): 352.84e6}
-
-
-def _peaks() -> dict:
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        d = json.load(open(p))
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
-    except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "source": "fallback"}
-
-
+# ---------------------------------------------------------------------------
+# CPU oracle: the reported baseline and the reference arm
+# ---------------------------------------------------------------------------
 def _oracle_iters(name: str):
-    import glob
-
-    vals = []
-    for p in glob.glob(os.path.join(ROOT, "tests", "golden", f"{name}_col*.json")):
-        d = json.load(open(p))
-        if d.get("iters_1e-8", -1) > 0:
-            vals.append(d["iters_1e-8"])
+    vals = [r["iters_1e-8"] for r in goldens(name) if r.get("iters_1e-8", -1) > 0]
     if vals:
-        return float(np.mean(vals)), f"oracle step counts of {len(vals)} sampled columns, tests/golden"
+        return float(np.mean(vals)), f"mean oracle step count at 1e-8 of {len(vals)} stored columns (tests/golden)"
     return 4000.0, "no oracle step counts stored; nominal 4000"
 
 
-def run_reference(args):
-    """The CPU oracle on the host cores: each step a bounded sample."""
-    wl, sys_, eps, cols, eta = make_workload(args.workload, args.seed)
+def oracle_batch_sample(sys_, eps, cols, eta, n_cols: int, n_steps: int, threads: int):
+    """Seconds per column-step of the batched oracle (oracle/krylov.py
+    lanczos_batch, C loops with OpenMP) on n_cols columns for n_steps steps."""
     from oracle import krylov
     from paper_1609_08377_gb300 import synthetic as syn
 
+    used = krylov.set_threads(threads)
+    c = np.asarray(cols[:n_cols])
+    zs = [syn.shifts(eps, float(e)) for e in eta[:n_cols]]
+    t0 = time.perf_counter()
+    krylov.lanczos_batch(sys_.A, sys_.B, c, zs, tol=1e-30, max_iter=n_steps, check_every=10 ** 9)
+    dt = time.perf_counter() - t0
+    return dt / (n_cols * n_steps), used, dt
+
+
+def oracle_rate(sys_, eps, cols, eta, mean_iters: float) -> dict:
+    """The oracle as it stands on the host cores, on bounded samples: the
+    one-column NumPy B-Lanczos on one core, and the batched C oracle on every
+    core; each scaled by the GPU solver's mean step count."""
+    from oracle import krylov
+    from paper_1609_08377_gb300 import synthetic as syn
+
+    S = len(eps)
+    j = int(cols[0])
+    z = syn.shifts(eps, float(eta[0]))
+    t0 = time.perf_counter()
+    krylov.lanczos_column(sys_.A, sys_.B, j, z, tol=1e-30, max_iter=2, check_every=10 ** 9)
+    t_probe = (time.perf_counter() - t0) / 3.0
+    n = int(max(3, min(300, 12.0 / max(t_probe, 1e-6))))
+    t0 = time.perf_counter()
+    krylov.lanczos_column(sys_.A, sys_.B, j, z, tol=1e-30, max_iter=n, check_every=10 ** 9)
+    dt1 = time.perf_counter() - t0
+    one = S / (dt1 / (n + 1) * max(mean_iters, 1.0))
+    ncores = os.cpu_count() or 1
+    per, used, dt = oracle_batch_sample(sys_, eps, cols, eta, 32, 20, ncores)
+    allc = S / (per * max(mean_iters, 1.0))
+    return {"value": allc, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"batched oracle B-Lanczos (FP64, C loops, OpenMP on {used} threads): 32 columns x 20 "
+                      f"Lanczos steps in {dt:.1f} s, scaled by the GPU solver's mean {mean_iters:.0f} steps per "
+                      f"column and {S} shifts per column",
+            "single_core": {"value": one, "unit": UNIT, "cores": 1,
+                            "sample": f"one-column NumPy/SciPy oracle: {n} Lanczos steps of column {j} in "
+                                      f"{dt1:.1f} s, scaled the same way"}}
+
+
+def run_reference(args):
+    """The CPU oracle on the host cores: each step a bounded sample (the
+    batched oracle, all cores, a few Lanczos steps of a batch of columns),
+    scaled by the oracle's own step count per column at 1e-8."""
+    wl, sys_, eps, cols, eta = make_workload(args.workload, args.seed)
     S = eps.size
-    steps_budget = 20          # Lanczos steps per bench step (bounded sample)
-    # A column of this workload takes the oracle far longer than a bench step, so
-    # its cost per column is its measured cost per Lanczos step times the number
-    # of steps the oracle itself needed to reach 1e-8 on sampled columns of the
-    # same workload (tests/golden, written by tests/golden/make_golden.py).
     mean_iters, src = _oracle_iters(wl.name)
+    ncores = os.cpu_count() or 1
+    n_cols, n_steps = 32, 10
     for b in range(args.warmup):
-        j = int(cols[b])
-        krylov.lanczos_column(sys_.A, sys_.B, j, syn.shifts(eps, float(eta[b])), tol=1e-30,
-                              max_iter=2, check_every=10 ** 9)
-    t = 0.0
+        oracle_batch_sample(sys_, eps, cols[b * n_cols:], eta[b * n_cols:], n_cols, 2, ncores)
+    t, used = 0.0, 1
     for i in range(args.steps):
         b = args.warmup + i
-        j = int(cols[b])
-        t0 = time.perf_counter()
-        krylov.lanczos_column(sys_.A, sys_.B, j, syn.shifts(eps, float(eta[b])), tol=1e-30,
-                              max_iter=steps_budget, check_every=10 ** 9)
-        t += time.perf_counter() - t0
-    per_step = t / (args.steps * (steps_budget + 1))
-    value = S / (per_step * mean_iters)
+        _, used, dt = oracle_batch_sample(sys_, eps, cols[b * n_cols:], eta[b * n_cols:], n_cols, n_steps, ncores)
+        t += dt
+    per = t / (args.steps * n_cols * n_steps)
+    value = S / (per * mean_iters)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded C/H tight-binding-like pencil standing in for the paper's PPE structures)",
            "config": workload_config(wl, sys_, S, args.cols_per_step, args, 1),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{steps_budget} Lanczos steps of one column per step, scaled by "
-                                      f"{mean_iters:.0f} steps per column ({src})"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                            "sample": f"per step {n_steps} Lanczos steps of {n_cols} columns (batched oracle, "
+                                      f"OpenMP on {used} threads), scaled by {mean_iters:.0f} steps per column "
+                                      f"({src})"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

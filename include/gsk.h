@@ -57,6 +57,10 @@ extern "C" {
                                 residuals, Lanczos vectors, inner products) in double-float
                                 arithmetic: pairs of FP32 numbers, 48-bit significand */
 
+#define GSK_SPMM_AUTO 0      /* inner-CG products: the autotuner's pick, else staged up to 64 lanes (default) */
+#define GSK_SPMM_GATHER 1    /* every product by the per-atom gather kernel */
+#define GSK_SPMM_STAGED 2    /* FP32 inner-CG products: tile rows staged in shared memory (mixed modes) */
+
 #define GSK_SCHED_FIFO 0     /* columns enter the work queue in the given order */
 #define GSK_SCHED_LEARNED 1  /* longest predicted iteration count first (needs a model) */
 
@@ -98,6 +102,14 @@ typedef struct {
   int32_t max_inner;    /* CG iteration cap per B-solve pass; default 200 */
   int32_t use_graph;    /* 1 = run the solve as one captured CUDA graph with device-side loops (default) */
   void* stream;         /* cudaStream_t to run on; NULL = the legacy default stream */
+  int32_t spmm_kernel;  /* GSK_SPMM_AUTO (default), GSK_SPMM_GATHER or GSK_SPMM_STAGED: how the
+                           FP32 products with B of the mixed modes' inner CG run. The gather
+                           kernel reads every neighbour row per atom through the caches; the
+                           staged kernel cuts the atoms (space-filling-curve order) into tiles
+                           whose neighbour rows fit in shared memory and copies each tile's
+                           rows, values and indices there once, asynchronously, two tiles in
+                           flight. Both give the same product up to FP32 rounding order;
+                           GSK_SPMM_STAGED on a non-mixed solve returns GSK_ENOTSUP. */
 } gsk_options;
 
 /* Fill *opt with the defaults above. */
@@ -153,7 +165,10 @@ int gsk_solve(gsk_handle h, int32_t n_shifts, const double* z, const double* eta
  * Eq. EQ-FD-FUNC, evaluated without overflow).
  *   eps, w    host, S doubles: real parts of the shifts and quadrature weights
  *   G         device, n_elem*S complex doubles; rho device, n_elem doubles
- *   stream    cudaStream_t or NULL. Asynchronous on that stream. */
+ *   stream    cudaStream_t or NULL. Asynchronous on that stream; eps and w
+ *             are copied from pageable host memory with cudaMemcpyAsync, so
+ *             the call is not meant to be recorded into a CUDA graph (a
+ *             captured copy would read the host arrays at replay time). */
 int gsk_density(gsk_handle h, int64_t n_elem, int32_t n_shifts, const double* eps,
                 const double* w, double mu, double kT, const double* G, double* rho,
                 void* stream);
@@ -176,7 +191,9 @@ int gsk_density(gsk_handle h, int64_t n_elem, int32_t n_shifts, const double* ep
  *   G, rho    device buffers on the current device, as for gsk_density
  *   stream    cudaStream_t or NULL; the work is asynchronous on that stream
  * The first call on a device looks up the array's device address (once per
- * device, with that device current). All calls share the array: each call
+ * device, with that device current) and keeps it for the life of the
+ * process, so after cudaDeviceReset on a device this entry point must not be
+ * called on that device again. All calls share the array: each call
  * overwrites the 3 * n_shifts entries it reads before it reads them, so
  * nothing has to start at zero, but calls whose work overlaps on the GPU
  * (for example on two streams) race on it and must be serialised by the
@@ -302,11 +319,14 @@ int gsk_marnoldi_projected(gsk_handle h, const double* box, int32_t kappa, int32
 int gsk_row_order(gsk_handle h, int32_t* row_lib);
 
 /* n_rep applications of the solver's block SpMM kernel, Y = S X with S = A
- * (which = 0) or B (which = 1), on W lanes (32, 64 or 128; 128 only for
+ * (which = 0) or B (which = 1 or 2), on W lanes (32, 64 or 128; 128 only for
  * FP32): the same kernel, launch shape and epilogue that gsk_solve runs, for
  * timing and for callers working in the library's row order. For B it is the
  * inner CG's kernel, which also sets a direction vector P = X (internal) and
- * forms the per-lane dot P.Y; for A it forms the dot X.Y.
+ * forms the per-lane dot P.Y; for A it forms the dot X.Y. For B, which = 1
+ * runs the per-atom gather kernel and which = 2 the staged kernel
+ * (GSK_MIXED only; it returns GSK_ETIMEOUT if one of its bounded waits gave
+ * up).
  *   precision GSK_FP64: X, Y are double; GSK_MIXED: X, Y are float
  *   X, Y      device, M x W row-major (lane fastest), rows in library order
  *   stream    cudaStream_t or NULL. Asynchronous on that stream. */
@@ -357,17 +377,39 @@ int gsk_mlp_train_step(int32_t n, const float* feat, const float* norm, const fl
 /* Install a trained model (host arrays) on the handle for GSK_SCHED_LEARNED. */
 int gsk_set_sched_model(gsk_handle h, const float* params, const float* norm);
 
-/* Autotuner of the lane width W (columns in flight). For each candidate W
- * (32, 64 and, in the mixed modes, 128) it times, with CUDA events, a
- * truncated solve (a few Lanczos steps) of the first columns of the set and
- * picks the W that minimises the estimated time of the whole set,
- * t_step(W) * max(n_cols / W, 2) in units of a column's mean step count (the
- * factor 2 accounts for the longest column of a set with mixed damping). The
- * result is cached on the handle for opt->precision and used by gsk_solve
- * whenever opt->batch_w is 0. Arguments as for gsk_solve; *best_w receives the
- * choice (host). Synchronous. */
+/* Autotuner of the lane width W (columns in flight) and, in the mixed modes,
+ * of the inner-CG product kernel. For each candidate W (32, 64 and, in the
+ * mixed modes, 128) and kernel (GSK_SPMM_GATHER, and GSK_SPMM_STAGED in the
+ * mixed modes) it times, with CUDA events, a truncated solve (24 Lanczos
+ * steps) of the first columns of the set and picks the pair that minimises
+ * the estimated time of the whole set, t_step * max(n_cols / W, 2) in units
+ * of a column's mean step count (the factor 2 accounts for the longest column
+ * of a set with mixed damping). The result is kept on the handle for
+ * opt->precision (and the best kernel for every W measured) and used by
+ * gsk_solve whenever opt->batch_w or opt->spmm_kernel is 0. If the
+ * environment variable GSK_TUNE_CACHE names a file, results are cached there
+ * across processes, one line per (M, nnz, atoms, precision, shifts, columns,
+ * GPU name, SM count): a hit skips the measurement; a miss appends a line.
+ * Arguments as for gsk_solve; *best_w receives the W chosen (host).
+ * Synchronous. */
 int gsk_autotune(gsk_handle h, int32_t n_shifts, const double* z, const double* eta, int32_t n_cols,
                  const int32_t* cols, const gsk_options* opt, int32_t* best_w);
+
+/* The last gsk_autotune result for a precision mode (host outputs, each may
+ * be NULL): the W and kernel chosen, whether they came from the cache file,
+ * and the candidates measured (up to 8: W, kernel, milliseconds per lock-step
+ * Lanczos step; none on a cache hit). */
+int gsk_autotune_result(gsk_handle h, int32_t precision, int32_t* w, int32_t* kernel, int32_t* from_cache,
+                        int32_t* n_cand, int32_t* cand_w, int32_t* cand_kernel, double* cand_ms_per_step);
+
+/* Measured FMA throughput of the current device, for the roofline of the
+ * ALU-bound kernels (the FP64 block products of gsk_marnoldi): every thread
+ * runs 8 independent FMA chains over a grid of 8 CTAs per SM; *tflops (host)
+ * receives the best of n_rep timed launches (CUDA events on stream, after one
+ * untimed launch) in TFLOP/s, 2 flops per FMA. precision: GSK_FP64 or
+ * GSK_MIXED (FP32). Allocates a small device buffer for the chains' results.
+ * Synchronous. The paper has no counterpart: it is a measurement tool. */
+int gsk_alu_peak(int32_t precision, int32_t n_rep, double* tflops, void* stream);
 
 /* Counters of the last gsk_solve on this handle. */
 typedef struct {
@@ -376,6 +418,7 @@ typedef struct {
   int64_t kernel_launches;   /* kernels the solve launched (graph nodes executed) */
   int32_t batch_w;           /* lanes used */
   int32_t used_graph;        /* 1 when the solve ran as one CUDA graph */
+  int32_t spmm_kernel;       /* GSK_SPMM_GATHER or GSK_SPMM_STAGED: kernel of the inner-CG products */
 } gsk_stats;
 
 /* Copy the counters of the last gsk_solve into *out (host). */

@@ -19,7 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgsk.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["gsk_solver.cu", "gsk_api.cu", "gsk_sched.cu", "gsk_traces.cu", "gsk_marnoldi.cu", "gsk_project.cu"]
+SOURCES = ["gsk_solver.cu", "gsk_api.cu", "gsk_sched.cu", "gsk_traces.cu", "gsk_marnoldi.cu", "gsk_project.cu",
+           "gsk_tiles.cu", "gsk_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

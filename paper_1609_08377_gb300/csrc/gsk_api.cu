@@ -464,6 +464,12 @@ int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_ha
     if (upload(h->d_warp_atoms, cut) != cudaSuccess) return fail(GSK_ECUDA);
     L.warp_atoms = h->d_warp_atoms.as<int32_t>();
   }
+  // tiles of the staged SpMM; an atom too large for one tile leaves them unbuilt
+  {
+    const int trc = gsk::build_tiles(h, roff, orb, nbr_ptr, nbr_mid, nbr_atom, val_ptr, nval);
+    if (trc == GSK_ENOMEM || trc == GSK_ECUDA) return fail(trc);
+    if (trc != GSK_OK) h->tiles.n_tiles = 0;
+  }
   L.atom_roff = h->d_atom_roff.as<int32_t>();
   L.atom_orb = h->d_atom_orb.as<int8_t>();
   L.nbr_ptr = h->d_nbr_ptr.as<int32_t>();
@@ -491,6 +497,22 @@ int gsk_autotune(gsk_handle h, int32_t n_shifts, const double* z, const double* 
                  const int32_t* cols, const gsk_options* opt, int32_t* best_w) {
   if (!h) return GSK_EINVAL;
   return gsk::autotune_impl(h, n_shifts, z, eta, n_cols, cols, opt, best_w);
+}
+
+int gsk_autotune_result(gsk_handle h, int32_t precision, int32_t* w, int32_t* kernel, int32_t* from_cache,
+                        int32_t* n_cand, int32_t* cand_w, int32_t* cand_kernel, double* cand_ms_per_step) {
+  if (!h || precision < GSK_FP64 || precision > GSK_MIXED_DF) return GSK_EINVAL;
+  const gsk::TuneRecord& r = h->tune[precision];
+  if (w) *w = r.w;
+  if (kernel) *kernel = r.kernel;
+  if (from_cache) *from_cache = r.from_cache;
+  if (n_cand) *n_cand = r.n_cand;
+  for (int i = 0; i < r.n_cand; ++i) {
+    if (cand_w) cand_w[i] = r.cand_w[i];
+    if (cand_kernel) cand_kernel[i] = r.cand_kernel[i];
+    if (cand_ms_per_step) cand_ms_per_step[i] = r.cand_ms_per_step[i];
+  }
+  return GSK_OK;
 }
 
 int gsk_row_order(gsk_handle h, int32_t* row_lib) {

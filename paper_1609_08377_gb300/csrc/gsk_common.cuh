@@ -43,6 +43,47 @@ struct Layout {
   const int32_t* warp_atoms;     // n_ctas * kWarps + 1: atoms [warp_atoms[w], warp_atoms[w+1]) of warp w
 };
 
+// Tiles of the staged SpMM (k_spmm_tiled). Atoms are cut, in library order,
+// into tiles of consecutive atoms; a tile's CTA copies into shared memory the
+// rows of every neighbour atom of the tile (its row union, contiguous row
+// runs cut into pieces of 8, 4, 2 or 1 rows), the tile's matrix values, local
+// neighbour indices and atom descriptors, and the tile's own rows of the CG
+// direction and of B p. Each consumer warp then runs a fixed, cost-balanced
+// list of the tile's atoms out of shared memory.
+constexpr int kTileLanes = 32;         // lanes per CTA (a W-lane batch uses W / 32 CTAs per tile)
+struct TileHead {                      // one per tile, 64 bytes
+  int32_t r0;                          // first own row (library order)
+  int32_t n_own;                       // own rows
+  int32_t n_atoms;                     // atoms
+  int32_t nbox;                        // row-run pieces of the row union
+  int32_t b0;                          // first piece
+  int32_t l0;                          // first local index (a multiple of 8)
+  int32_t nloc;                        // local indices (a multiple of 8)
+  int32_t d0;                          // first atom descriptor
+  int64_t v0;                          // first matrix value (a multiple of 4)
+  int32_t nval;                        // matrix values (a multiple of 4)
+  int32_t xrows;                       // shared rows of the row union
+  uint8_t wptr[16];                    // warp w runs descriptors [wptr[w], wptr[w+1]) (kWarps + 1 used)
+};
+static_assert(sizeof(TileHead) == 64, "TileHead is 64 bytes");
+// Atom descriptor (int4): x = orbitals | own row in the tile << 8 | shared
+// row of the atom's first row << 16; y = 4-orbital neighbours | 1-orbital
+// neighbour entries << 16; z = first value (from the tile's first);
+// w = first local index (from the tile's first).
+struct TileArgs {
+  int32_t n_tiles;
+  int32_t x_cap;                 // shared rows of the row union
+  int32_t own_cap;               // shared rows of each own-row buffer (P, Y)
+  int32_t v_cap;                 // shared matrix values (floats)
+  int32_t l_cap;                 // shared local indices (int16)
+  int32_t d_cap;                 // shared atom descriptors
+  const TileHead* head;          // n_tiles
+  const int2* box;               // row-run pieces: (first global row, first shared row | log2(rows) << 16)
+  const int16_t* loc;            // shared row of each neighbour entry's first row, tile by tile
+  const int4* desc;              // atom descriptors, tile by tile, in warp order
+  const int32_t* order;          // library atom of each descriptor
+};
+
 // Lane states of the batched solver.
 enum LaneState : int { LS_IDLE = 0, LS_SEED = 1, LS_ACTIVE = 2 };
 
@@ -84,6 +125,7 @@ struct LaneCtl {
   int* step;           // outer steps executed
   int* unfinished;     // lanes busy + jobs queued
   int* cg_total;       // total CG iterations (all passes), for statistics
+  int* err;            // set by a kernel whose bounded wait gave up
   unsigned int* red_counter;   // arrival counter of the second reduction level
   unsigned int* grp_counter;   // arrival counters of the first level (kMaxRedCtas / kRedGroup)
   double* partials;            // per-CTA partial sums (CTA * W + lane)
@@ -216,7 +258,8 @@ __device__ __forceinline__ double fold_rows(const double* __restrict__ src, int 
   const int l = threadIdx.x % W;
   const int pidx = threadIdx.x / W;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int b = b0 + pidx;
+  const bool in = threadIdx.x < kThreads;      // threads beyond kThreads (producer warps) add nothing
+  int b = in ? b0 + pidx : b1;
   for (; b + 3 * parts < b1; b += 4 * parts) {
     s0 += __ldcg(&src[(size_t)b * W + l]);
     s1 += __ldcg(&src[(size_t)(b + parts) * W + l]);
@@ -225,7 +268,7 @@ __device__ __forceinline__ double fold_rows(const double* __restrict__ src, int 
   }
   for (; b < b1; b += parts) s0 += __ldcg(&src[(size_t)b * W + l]);
   __syncthreads();
-  sm[pidx][l] = (s0 + s1) + (s2 + s3);
+  if (in) sm[pidx][l] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x < W)
@@ -233,30 +276,16 @@ __device__ __forceinline__ double fold_rows(const double* __restrict__ src, int 
   return t;
 }
 
-// Two-level deterministic reduction across the grid: each CTA writes its
+// Two-level deterministic reduction across the grid, from per-CTA sums:
+// thread t < W holds this CTA's sum for lane t in s. Each CTA writes its
 // per-lane partial; the last CTA to arrive in each group of kRedGroup CTAs
 // folds the group (fixed order); the last group to arrive folds the group
 // sums and runs the finalisation. Counters are reset by their last user.
-// mine[i] is this thread's partial for lane lane0 + i; within a warp the
-// threads with writer = true cover every lane exactly once.
-template <int L>
-__device__ __forceinline__ void lane_reduce_commit_at(const double (&mine)[L], const RedArgs& r, int lane0,
-                                                      bool writer) {
-  __shared__ double sm[kWarps][kMaxW];
+// sm is the CTA's fold scratch (kWarps x kMaxW doubles).
+__device__ __forceinline__ void cta_sums_commit(double s, const RedArgs& r, double (*sm)[kMaxW]) {
   __shared__ bool is_last;
   const int W = r.W;
-  const int warp = threadIdx.x >> 5;
-  if (writer) {
-#pragma unroll
-    for (int i = 0; i < L; ++i) sm[warp][lane0 + i] = mine[i];
-  }
-  __syncthreads();
-  if (threadIdx.x < W) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += sm[w][threadIdx.x];
-    r.c.partials[(size_t)blockIdx.x * W + threadIdx.x] = s;
-  }
+  if (threadIdx.x < W) r.c.partials[(size_t)blockIdx.x * W + threadIdx.x] = s;
   __threadfence();
   __syncthreads();
   const int grp = blockIdx.x / kRedGroup;
@@ -289,6 +318,29 @@ __device__ __forceinline__ void lane_reduce_commit_at(const double (&mine)[L], c
     finalize_all(r);
     *r.c.red_counter = 0u;
   }
+}
+
+// Per-lane reduction of a CTA followed by the grid commit. mine[i] is this
+// thread's partial for lane lane0 + i; within a warp the threads with
+// writer = true cover every lane exactly once; warps are folded in order.
+template <int L>
+__device__ __forceinline__ void lane_reduce_commit_at(const double (&mine)[L], const RedArgs& r, int lane0,
+                                                      bool writer) {
+  __shared__ double sm[kWarps][kMaxW];
+  const int W = r.W;
+  const int warp = threadIdx.x >> 5;
+  if (writer) {
+#pragma unroll
+    for (int i = 0; i < L; ++i) sm[warp][lane0 + i] = mine[i];
+  }
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < W) {
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += sm[w][threadIdx.x];
+  }
+  __syncthreads();
+  cta_sums_commit(s, r, sm);
 }
 
 template <int L>

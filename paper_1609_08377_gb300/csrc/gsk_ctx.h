@@ -10,6 +10,13 @@
 
 namespace gsk {
 
+// Result of one gsk_autotune call: the pick and every candidate measured.
+struct TuneRecord {
+  int w = 0, kernel = 0, from_cache = 0, n_cand = 0;
+  int cand_w[8] = {0}, cand_kernel[8] = {0};
+  double cand_ms_per_step[8] = {0}, cand_estimate[8] = {0};
+};
+
 // Device buffer that grows on demand and is owned by the handle.
 struct DevBuf {
   void* ptr = nullptr;
@@ -64,6 +71,11 @@ struct gsk_ctx {
   gsk::DevBuf d_atom_roff, d_atom_orb, d_nbr_ptr, d_nbr_mid, d_nbr_roff, d_val_ptr, d_warp_atoms;
   gsk::DevBuf d_A64, d_B64, d_A32, d_B32, d_A2, d_B2;   // FP64, FP32, FP32 pairs (hi, lo)
 
+  // tiles of the staged SpMM (built at creation; n_tiles == 0: not available)
+  gsk::TileArgs tiles{};
+  gsk::DevBuf d_tile_head, d_box, d_loc, d_desc, d_order;
+  int64_t tile_boxes = 0;  // row-run pieces of all row unions (statistics)
+
   gsk_stats last{};
 
   // learned scheduler
@@ -73,8 +85,11 @@ struct gsk_ctx {
   gsk::DevBuf ws_sched;           // feature / prediction scratch
   bool sched_ready = false;
 
-  // autotuned lane width per precision mode (0: not tuned)
+  // autotuned lane width per precision mode (0: not tuned) and inner-CG
+  // product kernel per precision mode and lane width 32 / 64 / 128 (0: not tuned)
   int tuned_w[3] = {0, 0, 0};
+  int tuned_kernel[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  gsk::TuneRecord tune[3];     // the autotuner's last result per precision mode
 
   // solver workspace (grown on demand)
   gsk::DevBuf ws_vec;      // Lanczos / CG vectors
@@ -90,7 +105,8 @@ struct gsk_ctx {
   ~gsk_ctx() {
     gsk::DevBuf* all[] = {&d_atom_roff, &d_atom_orb, &d_nbr_ptr, &d_nbr_mid, &d_nbr_roff, &d_val_ptr, &d_warp_atoms,
                           &d_A64, &d_B64, &d_A32, &d_B32, &d_A2, &d_B2, &ws_vec, &ws_lane, &ws_jobs,
-                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune, &ws_ma, &ws_proj};
+                          &ws_shift, &ws_gstage, &ws_misc, &d_rowfeat, &d_sched_params, &d_sched_norm, &ws_sched, &ws_tune, &ws_ma, &ws_proj,
+                          &d_tile_head, &d_box, &d_loc, &d_desc, &d_order};
     for (auto* b : all) b->release();
   }
 };
@@ -108,5 +124,27 @@ int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int
 int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
               void* stream);
 size_t spmm64_ws_bytes(const gsk_ctx* h);
+// Host plan of the staged SpMM's tiles (see TileArgs), from the host copy of
+// the block layout (atoms in library order).
+struct TilePlan {
+  int32_t n_tiles = 0, x_cap = 0, own_cap = 0, v_cap = 0, l_cap = 0, d_cap = 0;
+  std::vector<int32_t> tile_atom;     // n_tiles + 1 (atom ranges, for checks)
+  std::vector<TileHead> head;
+  std::vector<int2> box;
+  std::vector<int16_t> loc;
+  std::vector<int4> desc;
+  std::vector<int32_t> desc_atom;     // library atom of each descriptor (for checks)
+};
+// Returns GSK_OK, or GSK_ENOTSUP when one atom alone exceeds a capacity.
+int plan_tiles(const std::vector<int32_t>& roff, const std::vector<int8_t>& orb,
+               const std::vector<int32_t>& nbr_ptr, const std::vector<int32_t>& nbr_mid,
+               const std::vector<int32_t>& nbr_atom, const std::vector<int64_t>& val_ptr, int64_t n_vals,
+               TilePlan& plan);
+// Tiles of the staged SpMM uploaded to the handle. Returns GSK_OK,
+// GSK_ENOTSUP (see plan_tiles), GSK_ENOMEM or GSK_ECUDA.
+int build_tiles(gsk_ctx* h, const std::vector<int32_t>& roff, const std::vector<int8_t>& orb,
+                const std::vector<int32_t>& nbr_ptr, const std::vector<int32_t>& nbr_mid,
+                const std::vector<int32_t>& nbr_atom, const std::vector<int64_t>& val_ptr, int64_t n_vals);
+
 int spmm64_dot(gsk_ctx* h, int which, int W, const double* X, double* Y, double* dots, void* ws, cudaStream_t s);
 }

@@ -28,6 +28,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -234,6 +238,12 @@ template <typename T>
 __device__ __forceinline__ T fmadd(T a, T b, T c) { return fma(a, b, c); }
 template <>
 __device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Prefetch of a contiguous range into L2 (a hint: it never faults on the
+// range given, which must be 16-byte aligned with a size multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Block kernels of the SpMM: one neighbour block times L lanes of X.
 // 4-orbital row atom, 4-orbital neighbour: 4 X rows, 4 value columns.
@@ -578,6 +588,350 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
 #pragma unroll
   for (int i = 0; i < L; ++i) d[i] = double(dot[i]);
   lane_reduce_commit_at<L>(d, a.red, lane0, writer);
+}
+
+// ===========================================================================
+// K1t: staged block SpMM for the FP32 inner CG (SP_CG form of k_spmm).
+// ===========================================================================
+// One CTA per SM works through a static list of items (tile, lane quarter):
+// a W-lane batch runs W/32 lane quarters per tile, and gridDim.x is a
+// multiple of W/32, so a CTA keeps one quarter q = blockIdx.x % (W/32).
+// kProducers producer warps fill two shared-memory stages in turn: the row
+// union of X = r and the tile's own rows of P and Y by 16-byte asynchronous
+// copies (cp.async, 4 rows x 128 bytes per warp instruction), and the tile's
+// matrix values, local neighbour indices and atom descriptors by 1-D TMA bulk
+// copies, all completing on the stage's "full" mbarrier. kWarps consumer
+// warps run each item's fixed atom lists out of the stage -- four groups of 8
+// threads take every fourth neighbour block of an atom, the groups are
+// combined by shuffles, and group g writes own row g: p <- r + b p,
+// B p <- B r + b B p, with the dot p.(B p) kept per lane -- and arrive on the
+// stage's "empty" mbarrier, after which the producers refill it with the item
+// two ahead. So one item's copies run while the previous one is computed, and
+// a warp may start an item while slower warps finish the one before. Every
+// wait is bounded; a wait that gives up sets *err and the waiting warp stops.
+struct SpmmStagedArgs {
+  Layout g;
+  TileArgs t;
+  const float* val;      // FP32 values of B in the block layout
+  const float* X;        // r (gathered)
+  float* P;              // CG direction
+  float* Y;              // B p
+  int W;                 // lanes of the batch
+  int nq;                // W / 32
+  int* err;
+  RedArgs red;
+};
+
+constexpr int kProducers = 8;                                 // producer warps of the staged kernel
+constexpr int kStagedThreads = kThreads + 32 * kProducers;   // kWarps consumer warps + the producers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Test of a phase; a thread whose phase is still open is suspended for up to
+// about 0.5 us (woken early when the phase completes) instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(500)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity; gives up after about 2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > 4000000000LL) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// 16-byte asynchronous global -> shared copy (L2 only), and the arrival on an
+// mbarrier once all of this thread's earlier copies have landed (the arrival
+// is counted in the barrier's expected count).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fma_col(float (&acc)[4][4], const float4 c, const float4 x) {
+  const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    acc[0][i] = fmaf(c.x, xs[i], acc[0][i]);
+    acc[1][i] = fmaf(c.y, xs[i], acc[1][i]);
+    acc[2][i] = fmaf(c.z, xs[i], acc[2][i]);
+    acc[3][i] = fmaf(c.w, xs[i], acc[3][i]);
+  }
+}
+
+// Shared-memory layout of one stage (offsets in bytes from the stage base).
+struct StageLayout {
+  uint32_t x, p, y, v, l, d, hdr, bytes;
+  __host__ __device__ StageLayout(const TileArgs& t) {
+    x = 0;
+    p = x + (uint32_t)t.x_cap * kTileLanes * sizeof(float);
+    y = p + (uint32_t)t.own_cap * kTileLanes * sizeof(float);
+    v = y + (uint32_t)t.own_cap * kTileLanes * sizeof(float);
+    l = v + (uint32_t)t.v_cap * sizeof(float);
+    d = l + (uint32_t)t.l_cap * sizeof(int16_t);
+    hdr = d + (uint32_t)t.d_cap * sizeof(int4);
+    bytes = (hdr + sizeof(TileHead) + 127u) / 128u * 128u;
+  }
+};
+
+__global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmStagedArgs a) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ double sred[kWarps][kMaxW];
+  __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2];
+  const StageLayout SL(a.t);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x % a.nq;      // lane quarter of this CTA
+  const int qlane = q * kTileLanes;
+  const int n_items = a.t.n_tiles * a.nq;
+  const int n_mine = blockIdx.x < n_items ? (n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&full_bar[s], 32 * kProducers + 1);   // every producer thread's copies + the bulk copies
+      mbar_init(&empty_bar[s], kWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  float dot[4] = {0.f, 0.f, 0.f, 0.f};
+  const int grp = (lane >> 3);          // consumers: 4 groups of 8 threads share one atom
+  const int lane0 = (lane & 7) * 4;     // 4 lanes per thread
+  bool ok = true;
+  if (warp >= kWarps) {
+    // ---------------- producers ----------------
+    const int pw = warp - kWarps;         // producer warp pw copies boxes pw, pw + kProducers, ...
+    int issued = 0;
+    const int sub = lane >> 3, ch = (lane & 7) * 4;
+    // the next item's header and this warp's first 32 boxes are loaded one
+    // item ahead, so their latency overlaps the wait for a free stage
+    TileHead hd_next;
+    int2 box_next = make_int2(0, 0);
+    auto fetch = [&](int j) {
+      hd_next = a.t.head[(blockIdx.x + j * gridDim.x) / a.nq];
+      const int nm = hd_next.nbox > pw ? (hd_next.nbox - pw + kProducers - 1) / kProducers : 0;
+      box_next = lane < nm ? a.t.box[hd_next.b0 + pw + kProducers * lane] : make_int2(0, 0);
+    };
+    if (n_mine > 0) fetch(0);
+    for (int j = 0; j < n_mine && ok; ++j) {
+      const int s = j & 1;
+      unsigned char* st = sm_raw + (size_t)s * SL.bytes;
+      const TileHead hd = hd_next;
+      const int2 box0 = box_next;
+      if (j + 1 < n_mine) fetch(j + 1);
+      if (j >= 2) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty_bar[s], ((j >> 1) - 1) & 1));  // item j-2 consumed
+      if (!ok) break;
+      // the consumers' generic reads of this stage are ordered before the async writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (pw == 0 && lane == 0) {
+        *reinterpret_cast<TileHead*>(st + SL.hdr) = hd;
+        const uint32_t bytes = (uint32_t)hd.nval * sizeof(float) + (uint32_t)hd.nloc * sizeof(int16_t) +
+                               (uint32_t)hd.n_atoms * sizeof(int4);
+        mbar_expect_tx(&full_bar[s], bytes);     // releases the header store with the arrival
+        bulk_copy(st + SL.v, a.val + hd.v0, (uint32_t)hd.nval * sizeof(float), &full_bar[s]);
+        bulk_copy(st + SL.l, a.t.loc + hd.l0, (uint32_t)hd.nloc * sizeof(int16_t), &full_bar[s]);
+        bulk_copy(st + SL.d, a.t.desc + hd.d0, (uint32_t)hd.n_atoms * sizeof(int4), &full_bar[s]);
+      }
+      // row union of X: 4 rows x 8 chunks of 16 bytes per warp instruction; this
+      // warp copies boxes pw, pw + kProducers, ... (32 of them per register load)
+      float* sX = reinterpret_cast<float*>(st + SL.x);
+      const int nmine = hd.nbox > pw ? (hd.nbox - pw + kProducers - 1) / kProducers : 0;
+      for (int k0 = 0; k0 < nmine; k0 += 32) {
+        int2 mybox = box0;
+        if (k0 > 0) mybox = (k0 + lane < nmine) ? a.t.box[hd.b0 + pw + kProducers * (k0 + lane)] : make_int2(0, 0);
+        const int kn = min(32, nmine - k0);
+        for (int k = 0; k < kn; ++k) {
+          const int g0 = __shfl_sync(0xffffffffu, mybox.x, k);
+          const int code = __shfl_sync(0xffffffffu, mybox.y, k);
+          const int hgt = 1 << (code >> 16), s0 = code & 0xffff;
+          for (int r = sub; r < hgt; r += 4)
+            cp_async16(sX + (s0 + r) * kTileLanes + ch, a.X + (size_t)(g0 + r) * a.W + qlane + ch);
+        }
+      }
+      // own rows of P and Y
+      float* sP = reinterpret_cast<float*>(st + SL.p);
+      float* sYs = reinterpret_cast<float*>(st + SL.y);
+      for (int r = pw * 4 + sub; r < hd.n_own; r += 4 * kProducers) {
+        const size_t g = (size_t)(hd.r0 + r) * a.W + qlane + ch;
+        cp_async16(sP + r * kTileLanes + ch, a.P + g);
+        cp_async16(sYs + r * kTileLanes + ch, a.Y + g);
+      }
+      cp_async_arrive(&full_bar[s]);
+      issued = j + 1;
+    }
+    // before exiting, every copy issued into this CTA's shared memory has landed
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (lane == 0)
+      for (int j = max(0, issued - 2); j < issued; ++j)
+        if (!mbar_wait_bounded(&full_bar[j & 1], (j >> 1) & 1)) ok = false;
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok && lane == 0) atomicExch(a.err, 1);
+  } else {
+    // ---------------- consumers ----------------
+    float cb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cb[i] = (float)a.red.c.cg_b[qlane + lane0 + i];
+    for (int j = 0; j < n_mine; ++j) {
+      const int s = j & 1;
+      const unsigned char* st = sm_raw + (size_t)s * SL.bytes;
+      if (!mbar_wait_bounded(&full_bar[s], (j >> 1) & 1)) {
+        ok = false;
+        break;
+      }
+      const TileHead* shd = reinterpret_cast<const TileHead*>(st + SL.hdr);
+      const float* sX = reinterpret_cast<const float*>(st + SL.x);
+      const float* sP = reinterpret_cast<const float*>(st + SL.p);
+      const float* sY = reinterpret_cast<const float*>(st + SL.y);
+      const float* sV = reinterpret_cast<const float*>(st + SL.v);
+      const int16_t* sL = reinterpret_cast<const int16_t*>(st + SL.l);
+      const int4* sD = reinterpret_cast<const int4*>(st + SL.d);
+      const int r0 = shd->r0;
+      const int k1 = shd->wptr[warp + 1];
+      for (int k = shd->wptr[warp]; k < k1; ++k) {
+        const int4 d = sD[k];
+        const int oI = d.x & 0xff;
+        const int prow = (d.x >> 8) & 0xff;
+        const int xown = d.x >> 16;
+        const int n4 = d.y & 0xffff, n1 = d.y >> 16;
+        const float* v = sV + d.z;
+        const int16_t* lc = sL + d.w;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[r][i] = 0.f;
+        if (oI == 4) {
+#pragma unroll 2
+          for (int t = grp; t < n4; t += 4) {
+            const float* xp = sX + lc[t] * kTileLanes + lane0;
+            const float4 x0 = lds4(xp), x1 = lds4(xp + kTileLanes), x2 = lds4(xp + 2 * kTileLanes),
+                         x3 = lds4(xp + 3 * kTileLanes);
+            const float* vb = v + t * 16;
+            fma_col(acc, lds4(vb + 12), x3);
+            fma_col(acc, lds4(vb + 8), x2);
+            fma_col(acc, lds4(vb + 4), x1);
+            fma_col(acc, lds4(vb), x0);
+          }
+          const float* vh = v + n4 * 16;
+#pragma unroll 2
+          for (int t = grp; t < n1; t += 4)
+            fma_col(acc, lds4(vh + t * 4), lds4(sX + lc[n4 + t] * kTileLanes + lane0));
+        } else {
+#pragma unroll 2
+          for (int t = grp; t < n4; t += 4) {
+            const float* xp = sX + lc[t] * kTileLanes + lane0;
+            const float4 c = lds4(v + t * 4);
+            const float4 x0 = lds4(xp), x1 = lds4(xp + kTileLanes), x2 = lds4(xp + 2 * kTileLanes),
+                         x3 = lds4(xp + 3 * kTileLanes);
+            const float a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w},
+                        a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              acc[0][i] = fmaf(c.x, a0[i], fmaf(c.y, a1[i], fmaf(c.z, a2[i], fmaf(c.w, a3[i], acc[0][i]))));
+          }
+          const float* vh = v + n4 * 4;
+          const int nqd = n1 / 4;
+#pragma unroll 2
+          for (int qd = grp; qd < nqd; qd += 4) {
+            const int16_t* lq = lc + n4 + 4 * qd;
+            const float4 c = lds4(vh + 4 * qd);
+            const float4 x0 = lds4(sX + lq[0] * kTileLanes + lane0), x1 = lds4(sX + lq[1] * kTileLanes + lane0),
+                         x2 = lds4(sX + lq[2] * kTileLanes + lane0), x3 = lds4(sX + lq[3] * kTileLanes + lane0);
+            const float a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w},
+                        a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              acc[0][i] = fmaf(c.x, a0[i], fmaf(c.y, a1[i], fmaf(c.z, a2[i], fmaf(c.w, a3[i], acc[0][i]))));
+          }
+        }
+        if (oI == 4) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              acc[r][i] += __shfl_xor_sync(0xffffffffu, acc[r][i], 8);
+              acc[r][i] += __shfl_xor_sync(0xffffffffu, acc[r][i], 16);
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[0][i] += __shfl_xor_sync(0xffffffffu, acc[0][i], 8);
+            acc[0][i] += __shfl_xor_sync(0xffffffffu, acc[0][i], 16);
+          }
+        }
+        if (grp < oI) {
+          float br[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            br[i] = grp == 0 ? acc[0][i] : grp == 1 ? acc[1][i] : grp == 2 ? acc[2][i] : acc[3][i];
+          const int pr = prow + grp;
+          const float4 ro = lds4(sX + (xown + grp) * kTileLanes + lane0);
+          const float4 po = lds4(sP + pr * kTileLanes + lane0);
+          const float4 so = lds4(sY + pr * kTileLanes + lane0);
+          const float rv[4] = {ro.x, ro.y, ro.z, ro.w}, pv[4] = {po.x, po.y, po.z, po.w},
+                      sv[4] = {so.x, so.y, so.z, so.w};
+          float pn[4], yn[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const bool fresh = (cb[i] == 0.f);
+            pn[i] = fresh ? rv[i] : fmaf(cb[i], pv[i], rv[i]);
+            yn[i] = fresh ? br[i] : fmaf(cb[i], sv[i], br[i]);
+            dot[i] = fmaf(pn[i], yn[i], dot[i]);
+          }
+          const size_t base = (size_t)(r0 + pr) * a.W + qlane + lane0;
+          *reinterpret_cast<float4*>(a.P + base) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+          *reinterpret_cast<float4*>(a.Y + base) = make_float4(yn[0], yn[1], yn[2], yn[3]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[s]);    // this warp is done with the stage
+    }
+    if (!ok && lane == 0) atomicExch(a.err, 1);
+  }
+  // per-lane dot: groups, then consumer warps in order, then the grid reduction
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    dot[i] += __shfl_xor_sync(0xffffffffu, dot[i], 8);
+    dot[i] += __shfl_xor_sync(0xffffffffu, dot[i], 16);
+  }
+  if (warp < kWarps && grp == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sred[warp][lane0 + i] = (double)dot[i];
+  }
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x < a.W && threadIdx.x / kTileLanes == q) {
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sum += sred[w][threadIdx.x % kTileLanes];
+  }
+  __syncthreads();
+  cta_sums_commit(sum, a.red, sred);
 }
 
 // Double-float SpMM: Y = S X (SP_DOT: X = q in double-float, Y double-float,
@@ -1301,6 +1655,10 @@ struct Plan {
   SpmmArgs<double, float, float> spR;
   SpmmDfArgs<float2> spAdf;
   SpmmDfArgs<float> spRdf;
+  int spmm_kind = GSK_SPMM_GATHER;    // kernel of the FP32 inner-CG products
+  int grid_staged = 1;
+  unsigned staged_smem = 0;
+  SpmmStagedArgs spS;
   VecArgs upd, cgu[2], dot, fin;
   ShiftArgs sh;
   PrimeArgs prime;
@@ -1355,7 +1713,10 @@ cudaError_t launch_cg_iteration(const Plan& P, Launcher& la, int pass) {
     GSK_CUDA_TRY(la(K::spmm64cg, dim3(P.grid_rows), blk, P.spB64));
     GSK_CUDA_TRY(la(K::cgu64, dim3(P.grid_vec), blk, P.cgu[0]));
   } else {
-    GSK_CUDA_TRY(la(K::spmm32cg, dim3(P.grid_rows), blk, P.spB32[pass]));
+    if (P.spmm_kind == GSK_SPMM_STAGED)
+      GSK_CUDA_TRY(la(k_spmm_staged, dim3(P.grid_staged), dim3(kStagedThreads), P.spS, P.staged_smem));
+    else
+      GSK_CUDA_TRY(la(K::spmm32cg, dim3(P.grid_rows), blk, P.spB32[pass]));
     GSK_CUDA_TRY(la(K::cgu32, dim3(P.grid_vec), blk, P.cgu[pass]));
   }
   return cudaSuccess;
@@ -1437,7 +1798,7 @@ cudaError_t build_graph(Plan& P, cudaGraphExec_t* exec) {
     gc.h_inner2 = h_in2;
     // propagate graph control into every argument block
     RedArgs* reds[] = {&P.spA.red, &P.spB64.red, &P.spB32[0].red, &P.spB32[1].red, &P.spR.red,
-                       &P.spAdf.red, &P.spRdf.red,
+                       &P.spAdf.red, &P.spRdf.red, &P.spS.red,
                        &P.upd.red, &P.cgu[0].red, &P.cgu[1].red,
                        &P.dot.red, &P.fin.red};
     for (RedArgs* r : reds) r->gc = gc;
@@ -1612,8 +1973,35 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   void* p = cgb + 3 * bcg;
   void* Bp = cgb + 4 * bcg;
 
+  // kernel of the FP32 inner-CG products (mixed modes) and its launch shape
+  if (opt.spmm_kernel < GSK_SPMM_AUTO || opt.spmm_kernel > GSK_SPMM_STAGED) return GSK_EINVAL;
+  {
+    int kind = opt.spmm_kernel;
+    if (!P.mixed || h->tiles.n_tiles == 0) {
+      if (kind == GSK_SPMM_STAGED) return GSK_ENOTSUP;
+      kind = GSK_SPMM_GATHER;
+    }
+    if (kind == GSK_SPMM_AUTO) {
+      // the autotuner's pick for this lane width, else the measured rule: the
+      // staged kernel up to 64 lanes, the gather kernel at 128
+      const int wi = W == 32 ? 0 : W == 64 ? 1 : 2;
+      kind = h->tuned_kernel[opt.precision][wi] != 0 ? h->tuned_kernel[opt.precision][wi]
+                                                     : (W <= 64 ? GSK_SPMM_STAGED : GSK_SPMM_GATHER);
+    }
+    if (kind == GSK_SPMM_STAGED) {
+      const int nq = W / kTileLanes;
+      P.grid_staged = std::min(h->tiles.n_tiles * nq, h->num_sms);
+      P.grid_staged = std::max(nq, P.grid_staged - P.grid_staged % nq);
+      P.staged_smem = 2u * StageLayout(h->tiles).bytes;
+      if (cudaFuncSetAttribute(k_spmm_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.staged_smem) !=
+          cudaSuccess)
+        return GSK_ECUDA;
+    }
+    P.spmm_kind = kind;
+  }
+
   // lane control block
-  const int n_red = std::max(P.grid_rows, P.grid_vec);
+  const int n_red = std::max(std::max(P.grid_rows, P.grid_vec), P.grid_staged);
   if (n_red > kMaxRedCtas) return GSK_ENOTSUP;
   const int n_grp_max = (kMaxRedCtas + kRedGroup - 1) / kRedGroup;
   const size_t lane_bytes = 64 * kMaxW * sizeof(double) + (size_t)n_red * kMaxW * sizeof(double) +
@@ -1633,6 +2021,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
     c.queue_head = scal + 0; c.cg_iter = scal + 1; c.step = scal + 2; c.unfinished = scal + 3;
     c.cg_total = scal + 4;
     c.red_counter = reinterpret_cast<unsigned int*>(scal + 5);
+    c.err = scal + 8;
     c.partials = reinterpret_cast<double*>(lb + o);
     o += (size_t)n_red * kMaxW * sizeof(double);
     c.grp_partials = reinterpret_cast<double*>(lb + o);
@@ -1727,6 +2116,18 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
              nullptr, nullptr, nullptr, red(FIN_ALPHA)};
   P.spRdf = {g, h->d_B2.as<float2>(), static_cast<const float*>(x), nullptr, reinterpret_cast<const float2*>(u),
              static_cast<float*>(r), static_cast<float*>(p), static_cast<float*>(x2), red(FIN_RESID)};
+  if (P.spmm_kind == GSK_SPMM_STAGED) {
+    P.spS.g = g;
+    P.spS.t = h->tiles;
+    P.spS.val = h->d_B32.as<float>();
+    P.spS.X = static_cast<const float*>(r);
+    P.spS.P = static_cast<float*>(p);
+    P.spS.Y = static_cast<float*>(Bp);
+    P.spS.W = W;
+    P.spS.nq = W / kTileLanes;
+    P.spS.err = c.err;
+    P.spS.red = red(FIN_CG_A);
+  }
   VecArgs va{};
   va.M = M; va.q = q; va.ring0 = ring0; va.ring1 = ring1; va.u = u;
   va.r = r; va.p = p; va.Bp = Bp; va.x = x; va.x2 = x2; va.step = c.step;
@@ -1782,10 +2183,11 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_it.data(), d_iters, n_cols * sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_st.data(), d_status, n_cols * sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_rs.data(), d_resid, n_cols * sizeof(double), cudaMemcpyDeviceToHost, stream);
-  int h_cnt[5] = {0, 0, 0, 0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, c.queue_head, 5 * sizeof(int), cudaMemcpyDeviceToHost, stream);
+  int h_cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, c.queue_head, 9 * sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GSK_ECUDA;
+  if (h_cnt[8] != 0) return GSK_ETIMEOUT;     // a bounded wait of the staged SpMM gave up
   {
     // scal layout: queue_head, cg_iter, step, unfinished, cg_total
     const int64_t steps = h_cnt[2], cgt = h_cnt[4];
@@ -1795,6 +2197,7 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
     h->last.kernel_launches = 3 + steps * per_step + cgt * 2;
     h->last.batch_w = W;
     h->last.used_graph = opt.use_graph ? 1 : 0;
+    h->last.spmm_kernel = P.spmm_kind;
   }
   if (iters) memcpy(iters, h_it.data(), n_cols * sizeof(int32_t));
   if (status) memcpy(status, h_st.data(), n_cols * sizeof(int32_t));
@@ -1811,13 +2214,17 @@ namespace gsk {
 
 int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
               void* stream) {
-  if ((which != 0 && which != 1) || (precision != GSK_FP64 && precision != GSK_MIXED) || n_rep < 0 || !X || !Y)
+  if (which < 0 || which > 2 || (precision != GSK_FP64 && precision != GSK_MIXED) || n_rep < 0 || !X || !Y)
     return GSK_EINVAL;
   if (W != 32 && W != 64 && W != 128) return GSK_EINVAL;
   if (precision == GSK_FP64 && W == 128) return GSK_ENOTSUP;
+  if (which == 2 && (precision != GSK_MIXED || h->tiles.n_tiles == 0)) return GSK_ENOTSUP;
   if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int grid = h->lay.n_ctas;
+  const int nq = W / kTileLanes;
+  int grid_t = std::min(h->tiles.n_tiles * nq, h->num_sms);
+  grid_t = std::max(nq, grid_t - grid_t % nq);
+  const int grid = which == 2 ? std::max(h->lay.n_ctas, grid_t) : h->lay.n_ctas;
   const int n_grp_max = (kMaxRedCtas + kRedGroup - 1) / kRedGroup;
   const size_t lane_bytes = 64 * kMaxW * sizeof(double) + (size_t)grid * kMaxW * sizeof(double) +
                             (size_t)n_grp_max * kMaxW * sizeof(double) + n_grp_max * sizeof(unsigned) + 256;
@@ -1825,7 +2232,7 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
   if (h->ws_lane.ensure(lane_bytes) != cudaSuccess) return GSK_ENOMEM;
   // direction vector of the CG form of the product (B): M x W, zero coefficient
   const size_t esz = precision == GSK_FP64 ? sizeof(double) : sizeof(float);
-  if (which == 1 && h->ws_misc.ensure((size_t)h->M * W * esz + 256) != cudaSuccess) return GSK_ENOMEM;
+  if (which >= 1 && h->ws_misc.ensure((size_t)h->M * W * esz + 256) != cudaSuccess) return GSK_ENOMEM;
   char* lb = h->ws_lane.as<char>();
   if (cudaMemsetAsync(lb, 0, lane_bytes, s) != cudaSuccess) return GSK_ECUDA;
   LaneCtl c{};
@@ -1840,7 +2247,35 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
   r.fin = FIN_SUM;
   r.W = W;
   const dim3 blk(kThreads), grd(grid);
-  void* P = which == 1 ? h->ws_misc.ptr : nullptr;
+  void* P = which >= 1 ? h->ws_misc.ptr : nullptr;
+  if (which == 2) {
+    // staged kernel: the caller's X and Y plus the internal direction vector
+    c.err = reinterpret_cast<int*>(lb + 2 * kMaxW * sizeof(double)) + 4;
+    r.c = c;
+    SpmmStagedArgs T;
+    T.g = h->lay;
+    T.t = h->tiles;
+    T.val = h->d_B32.as<float>();
+    T.X = static_cast<const float*>(X);
+    T.P = static_cast<float*>(P);
+    T.Y = static_cast<float*>(Y);
+    T.W = W;
+    T.nq = nq;
+    T.err = c.err;
+    T.red = r;
+    const unsigned smem = 2u * StageLayout(h->tiles).bytes;
+    if (cudaFuncSetAttribute(k_spmm_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GSK_ECUDA;
+    for (int i = 0; i < n_rep; ++i) {
+      k_spmm_staged<<<dim3(grid_t), dim3(kStagedThreads), smem, s>>>(T);
+      if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
+    }
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, c.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return GSK_ECUDA;
+    return herr ? GSK_ETIMEOUT : GSK_OK;
+  }
   for (int i = 0; i < n_rep; ++i) {
     if (precision == GSK_FP64) {
       SpmmArgs<double, double, double> a{h->lay, (which ? h->d_B64 : h->d_A64).as<double>(),
@@ -1920,10 +2355,44 @@ int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int
   if (opt.precision < GSK_FP64 || opt.precision > GSK_MIXED_DF) return GSK_EINVAL;
   if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(opt.stream);
+  TuneRecord& rec = h->tune[opt.precision];
+  rec = TuneRecord{};
+  // on-disk cache keyed by the pencil, the request and the GPU
+  char key[512];
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return GSK_ECUDA;
+    for (char* c = prop.name; *c; ++c)
+      if (*c == ' ' || *c == '\t') *c = '_';
+    snprintf(key, sizeof(key), "M=%d nnz=%lld natoms=%d precision=%d shifts=%d cols=%d gpu=%s sms=%d", h->M,
+             (long long)h->nnz, h->n_atoms, opt.precision, S, n_cols, prop.name, prop.multiProcessorCount);
+  }
+  const char* path = getenv("GSK_TUNE_CACHE");
+  if (path && *path) {
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+      const size_t bar = line.find(" | ");
+      if (bar == std::string::npos || line.compare(0, bar, key) != 0 || bar != strlen(key)) continue;
+      int w = 0, k = 0;
+      if (sscanf(line.c_str() + bar + 3, "W=%d kernel=%d", &w, &k) == 2 && (w == 32 || w == 64 || w == 128) &&
+          (k == GSK_SPMM_GATHER || k == GSK_SPMM_STAGED) && !(k == GSK_SPMM_STAGED && h->tiles.n_tiles == 0)) {
+        h->tuned_w[opt.precision] = w;
+        h->tuned_kernel[opt.precision][w == 32 ? 0 : w == 64 ? 1 : 2] = k;
+        rec.w = w;
+        rec.kernel = k;
+        rec.from_cache = 1;
+        *best_w = w;
+        return GSK_OK;
+      }
+    }
+  }
   const int cands[3] = {32, 64, 128};
   const int n_cand = (opt.precision == GSK_FP64) ? 2 : 3;
+  std::vector<int> kernels{GSK_SPMM_GATHER};
+  if (opt.precision != GSK_FP64 && h->tiles.n_tiles > 0) kernels.push_back(GSK_SPMM_STAGED);
   double best = 1e300;
-  int pick = 64;
+  int pick_w = 64, pick_k = GSK_SPMM_GATHER;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GSK_ECUDA;
   int rc = GSK_OK;
@@ -1937,36 +2406,61 @@ int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int
       rc = GSK_ENOMEM;
       break;
     }
-    gsk_options o = opt;
-    o.batch_w = W;
-    o.max_iter = 24;
-    o.tol = 1e-30;
-    o.sched = GSK_SCHED_FIFO;
-    double ms_per_step = 0.0;
-    for (int rep = 0; rep < 2 && rc == GSK_OK; ++rep) {     // first run warms up and builds nothing persistent
-      cudaEventRecord(e0, s);
-      rc = solve_impl(h, S, z, eta, n, cols, &o, h->ws_tune.as<double>(), nullptr, nullptr, nullptr);
-      cudaEventRecord(e1, s);
-      if (rc != GSK_OK) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = GSK_ECUDA;
-        break;
+    double best_k = 1e300;
+    for (int kern : kernels) {
+      gsk_options o = opt;
+      o.batch_w = W;
+      o.spmm_kernel = kern;
+      o.max_iter = 24;
+      o.tol = 1e-30;
+      o.sched = GSK_SCHED_FIFO;
+      double ms_per_step = 0.0;
+      for (int rep = 0; rep < 2 && rc == GSK_OK; ++rep) {     // the first run warms up
+        cudaEventRecord(e0, s);
+        rc = solve_impl(h, S, z, eta, n, cols, &o, h->ws_tune.as<double>(), nullptr, nullptr, nullptr);
+        cudaEventRecord(e1, s);
+        if (rc != GSK_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = GSK_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_per_step = ms / std::max<int64_t>(1, h->last.outer_steps);
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms_per_step = ms / std::max<int64_t>(1, h->last.outer_steps);
-    }
-    const double est = ms_per_step * std::max((double)n_cols / W, 2.0);
-    if (rc == GSK_OK && est < best) {
-      best = est;
-      pick = W;
+      if (rc != GSK_OK) break;
+      // estimated time of the whole set in units of a column's mean step count;
+      // the factor 2 covers the longest column of a set with mixed damping
+      const double est = ms_per_step * std::max((double)n_cols / W, 2.0);
+      if (rec.n_cand < (int)(sizeof(rec.cand_w) / sizeof(rec.cand_w[0]))) {
+        rec.cand_w[rec.n_cand] = W;
+        rec.cand_kernel[rec.n_cand] = kern;
+        rec.cand_ms_per_step[rec.n_cand] = ms_per_step;
+        rec.cand_estimate[rec.n_cand] = est;
+        ++rec.n_cand;
+      }
+      if (est < best_k) {
+        best_k = est;
+        h->tuned_kernel[opt.precision][ci] = kern;
+      }
+      if (est < best) {
+        best = est;
+        pick_w = W;
+        pick_k = kern;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != GSK_OK) return rc;
-  h->tuned_w[opt.precision] = pick;
-  *best_w = pick;
+  h->tuned_w[opt.precision] = pick_w;
+  rec.w = pick_w;
+  rec.kernel = pick_k;
+  if (path && *path) {
+    std::ofstream out(path, std::ios::app);
+    if (out) out << key << " | W=" << pick_w << " kernel=" << pick_k << "\n";
+  }
+  *best_w = pick_w;
   return GSK_OK;
 }
 

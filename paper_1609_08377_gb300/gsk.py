@@ -20,6 +20,7 @@ GSK_OK, GSK_EINVAL, GSK_ENOTSPD, GSK_ENOMEM, GSK_ECUDA, GSK_ETIMEOUT, GSK_ENOTSU
 GSK_CONVERGED, GSK_NOT_CONVERGED, GSK_BREAKDOWN, GSK_TIMEOUT = 0, 1, 2, 3
 GSK_FP64, GSK_MIXED, GSK_MIXED_DF = 0, 1, 2
 GSK_SCHED_FIFO, GSK_SCHED_LEARNED = 0, 1
+GSK_SPMM_AUTO, GSK_SPMM_GATHER, GSK_SPMM_STAGED = 0, 1, 2
 
 
 class GskError(RuntimeError):
@@ -30,7 +31,7 @@ class GskError(RuntimeError):
 
 class Stats(C.Structure):
     _fields_ = [("outer_steps", C.c_int64), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64),
-                ("batch_w", C.c_int32), ("used_graph", C.c_int32)]
+                ("batch_w", C.c_int32), ("used_graph", C.c_int32), ("spmm_kernel", C.c_int32)]
 
 
 class _Csr(C.Structure):
@@ -45,7 +46,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("batch_w", C.c_int32), ("refine", C.c_int32), ("sched", C.c_int32),
                 ("inner_tol", C.c_double), ("max_inner", C.c_int32), ("use_graph", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("spmm_kernel", C.c_int32)]
 
 
 def _load() -> C.CDLL:
@@ -67,6 +68,8 @@ def _load() -> C.CDLL:
         "gsk_row_order": (C.c_int, [P, P]),
         "gsk_spmm": (C.c_int, [P, I32, I32, I32, P, P, I32, P]),
         "gsk_density_noalloc": (C.c_int, [I64, I32, P, P, D, D, P, P, P]),
+        "gsk_alu_peak": (C.c_int, [I32, I32, P, P]),
+        "gsk_autotune_result": (C.c_int, [P, I32, P, P, P, P, P, P, P]),
         "gsk_features": (C.c_int, [P, I32, P, P, P, P]),
         "gsk_mlp_forward": (C.c_int, [I32, P, P, P, P, P]),
         "gsk_mlp_workspace_bytes": (C.c_size_t, [I32]),
@@ -117,7 +120,8 @@ def default_options(**kw) -> Options:
     o = Options()
     _lib.gsk_default_options(C.byref(o))
     names = {"precision": {"fp64": GSK_FP64, "mixed": GSK_MIXED, "mixed_df": GSK_MIXED_DF},
-             "sched": {"fifo": GSK_SCHED_FIFO, "learned": GSK_SCHED_LEARNED}}
+             "sched": {"fifo": GSK_SCHED_FIFO, "learned": GSK_SCHED_LEARNED},
+             "spmm_kernel": {"auto": GSK_SPMM_AUTO, "gather": GSK_SPMM_GATHER, "staged": GSK_SPMM_STAGED}}
     for k, v in kw.items():
         if v is None:
             continue
@@ -238,6 +242,21 @@ class Solver:
                                  C.byref(w)), "gsk_autotune")
         return int(w.value)
 
+    def autotune_result(self, precision) -> dict:
+        """gsk_autotune_result: the last autotuner pick and its candidates."""
+        if isinstance(precision, str):
+            precision = {"fp64": GSK_FP64, "mixed": GSK_MIXED, "mixed_df": GSK_MIXED_DF}[precision]
+        w, k, fc, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        cw = np.zeros(8, dtype=np.int32)
+        ck = np.zeros(8, dtype=np.int32)
+        cm = np.zeros(8, dtype=np.float64)
+        _check(_lib.gsk_autotune_result(self._h, int(precision), C.byref(w), C.byref(k), C.byref(fc), C.byref(n),
+                                        _ptr(cw), _ptr(ck), _ptr(cm)), "gsk_autotune_result")
+        names = {GSK_SPMM_GATHER: "gather", GSK_SPMM_STAGED: "staged"}
+        return {"W": int(w.value), "kernel": names.get(int(k.value), int(k.value)), "from_cache": bool(fc.value),
+                "candidates": [{"W": int(cw[i]), "kernel": names.get(int(ck[i]), int(ck[i])),
+                                "ms_per_step": float(cm[i])} for i in range(int(n.value))]}
+
     def density(self, G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=None) -> None:
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -342,6 +361,14 @@ def density_noalloc(G, eps, w, mu: float, kT: float, rho, n_elem: int, stream=No
 
 
 MLP_IN, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
+
+
+def alu_peak(precision: int, n_rep: int = 5, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device: gsk_alu_peak."""
+    out = C.c_double(0.0)
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_lib.gsk_alu_peak(int(precision), int(n_rep), C.byref(out), s), "gsk_alu_peak")
+    return float(out.value)
 
 
 def mlp_forward(n: int, feat, norm, params, y, stream=None) -> None:

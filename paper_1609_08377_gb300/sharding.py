@@ -28,6 +28,23 @@ def shard_columns(cols, rank: int, world: int) -> np.ndarray:
     return np.ascontiguousarray(cols[rank::world])
 
 
+def stratified_batches(n_chunks: int, n_take: int, rank: int, world: int, seed: int = 0) -> np.ndarray:
+    """Batch (chunk) indices of this rank for a benchmark over a column set
+    cut into n_chunks chunks of consecutive columns (in the learned scheduler's
+    longest-first order): n_take * world indices evenly spaced over
+    [0, n_chunks), dealt to the ranks round-robin, so every rank gets a
+    stratified sample of the set and no chunk is used twice as long as
+    n_take * world <= n_chunks; then shuffled (seeded) within the rank, so the
+    first (warm-up) batches are not all of one kind."""
+    total = n_take * world
+    if total > n_chunks:
+        raise ValueError(f"{n_take} batches on {world} ranks need {total} chunks; the set has {n_chunks}")
+    idx = np.floor((np.arange(total) + 0.5) * n_chunks / total).astype(np.int64)
+    mine = idx[rank::world]
+    rng = np.random.default_rng(seed + 1000 + rank)
+    return mine[rng.permutation(mine.size)]
+
+
 def allreduce_sum(x, dist=None, device="cpu") -> np.ndarray:
     """Sum of a host vector over all ranks (identity without a process group).
     The sum runs in FP64 on `device` (a CUDA device under NCCL)."""

@@ -1,8 +1,9 @@
-"""Multi-rank host logic of the benchmark on CPU (gloo, world size 2).
+"""Multi-rank host logic of the benchmark on CPU (gloo, world sizes 2 and 8).
 
 Columns are independent (Eq. TRACE-X-DECOMP of the paper), so ranks take
-disjoint column batches and the only collective is the max-over-ranks of the
-step time; both are checked here without a GPU.
+disjoint column batches and the only collectives are the max-over-ranks of
+the step time and the sum of per-shift traces; all are checked here without
+a GPU.
 """
 
 import os
@@ -23,15 +24,16 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, n_cols, C, n_batches, out):
+def _worker(rank, world, port, n_chunks, n_batches, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
+    from paper_1609_08377_gb300 import sharding
 
-    ranges = bench.rank_batches(n_cols, C, n_batches, rank, world)
+    mine = sharding.stratified_batches(n_chunks, n_batches, rank, world, 0).tolist()
     gathered = [None] * world
-    dist.all_gather_object(gathered, ranges)
+    dist.all_gather_object(gathered, mine)
     t = bench.max_over_ranks(1.5 + rank, dist, "cpu")
     if rank == 0:
         out.put((gathered, t))
@@ -39,28 +41,40 @@ def _worker(rank, world, port, n_cols, C, n_batches, out):
     dist.destroy_process_group()
 
 
-def test_two_ranks_disjoint_batches_and_max_time():
+@pytest.mark.parametrize("world,n_batches", [(2, 6), (8, 26)])
+def test_ranks_disjoint_stratified_batches_and_max_time(world, n_batches):
+    """The benchmark's batches: 16,384 columns in chunks of 32 (512 chunks);
+    every rank gets n_batches distinct chunks spread over the whole
+    longest-first order, no chunk twice across ranks; the job's step time is
+    the slowest rank's."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    n_cols, C, n_batches = 8192, 128, 6
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, n_cols, C, n_batches, q)) for r in range(2)]
+    n_chunks = 16384 // 32
+    procs = [ctx.Process(target=_worker, args=(r, world, port, n_chunks, n_batches, q)) for r in range(world)]
     for p in procs:
         p.start()
-    gathered, t = q.get(timeout=120)
+    gathered, t = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    assert t == 2.5
+    assert t == 1.5 + (world - 1)
     seen = set()
-    for ranges in gathered:
-        assert len(ranges) == n_batches
-        for a, b in ranges:
-            assert b - a == C
-            cols = set(range(a, b))
-            assert not (cols & seen)
-            seen |= cols
-    assert len(seen) == 2 * n_batches * C
+    for mine in gathered:
+        assert len(mine) == n_batches
+        assert all(0 <= k < n_chunks for k in mine)
+        # stratified: the rank's chunks span the order (first and last quarter both hit)
+        assert min(mine) < n_chunks // 4 and max(mine) >= 3 * n_chunks // 4
+        assert not (set(mine) & seen)
+        seen |= set(mine)
+    assert len(seen) == world * n_batches
+
+
+def test_stratified_batches_refuse_reuse():
+    from paper_1609_08377_gb300 import sharding
+
+    with pytest.raises(ValueError):
+        sharding.stratified_batches(100, 26, 0, 8)
 
 
 # ---------------------------------------------------------------------------
