@@ -64,6 +64,9 @@ def _parse():
     ap.add_argument("--no-graph", action="store_true", help="host-driven loop (for kernel-level profiling)")
     ap.add_argument("--no-extras", action="store_true", help="only the headline (no FP64, e2e, Arnoldi, CPU legs)")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--queue-cols", type=int, default=0,
+                    help="instead of the benchmark: one gsk_solve of this many columns of the workload's set "
+                         "through the device work queue, FIFO and learned order (lane utilisation)")
     return ap.parse_args()
 
 
@@ -253,6 +256,8 @@ def main():
         if rank != 0:
             return
         return run_reference(args)
+    if args.queue_cols > 0:
+        return queue_scale(args)
 
     import torch
 
@@ -419,7 +424,7 @@ def oracle_errors(solver, c, G, refs, eps, S, dev):
     return gerr, rerr
 
 
-def e2e_rate(solver, batches, timed, times, z, S, opts, dev, world, n: int = 4) -> dict:
+def e2e_rate(solver, batches, timed, times, z, S, opts, dev, world, n: int = 2) -> dict:
     """The same metric through the C ABI with host buffers: inputs from the
     host and G into pinned host memory, wall clock around each call, on n of
     the timed batches (evenly spaced); the device-timed rate of the same
@@ -528,13 +533,14 @@ def spmm_roofline(solver, sys_, W, kern, args, stream, dev) -> dict:
             "ms_per_launch": sec * 1e3, "alg_bytes_per_launch": int(alg), "peak_source": peaks["source"]}
 
 
+FP64_PEAK_TFLOPS = 1.25     # GB300 dense FP64 (profiling recipe); gsk_alu_peak's chains reach about 1.06
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # inner-CG product from one ncu capture per (workload, kernel, value bytes, W),
 # with the profiles/ summary that records it
 _NCU_TRAFFIC = {
-    ("ch100k", "staged", 4, 32): (None, ""),
+    ("ch100k", "staged", 4, 32): (212.54e6, "profiles/spmm_staged_ch100k_w32.md (ncu --set full, one launch)"),
 }
-_NCU_TRAFFIC = {k: v for k, v in _NCU_TRAFFIC.items() if v[0] is not None}
 
 
 def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
@@ -595,12 +601,13 @@ def marnoldi_rate(solver, sys_, dev, n_cols=256, nu=30) -> dict:
     return {"value": n_cols / (best / 1e3), "unit": "columns/s", "nu": nu, "columns": n_cols,
             "charge_sum_max_err": float(np.abs(charge.sum(axis=1) - 1.0).max()),
             "rank_min": int(rank.min()),
-            "roofline": {"bound": "alu", "achieved": flops / sec / 1e12, "peak": p64,
-                         "unit": "TFLOP/s", "frac": flops / sec / 1e12 / p64, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": flops / sec / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / sec / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                          "kernel": "k_spmm<double> A-product, W=64 (FP64 FMAs: 2 nnz W per launch)",
                          "ms_per_launch": sec * 1e3,
-                         "peak_source": "gsk_alu_peak: FP64 FMA chains measured in this run",
-                         "fp32_tflops": p32, "clocks": clk_rec},
+                         "peak_source": "GB300 FP64 rate of the profiling recipe (1.25 TFLOP/s); FMA chains "
+                                        "measured in this run given beside it",
+                         "fp64_fma_chains_tflops": p64, "fp32_fma_chains_tflops": p32, "clocks": clk_rec},
             "cpu_baseline": {"value": cpu, "unit": "columns/s", "cores": 1, "kind": "oracle",
                              "sample": "oracle multiple Arnoldi (NumPy/SciPy) on 2 of the columns"},
             "projected": proj}
@@ -625,6 +632,55 @@ def projected_rate(solver, sys_, cols, nu, dev):
     return {"value": pc.size / tp, "unit": "columns/s", "kappa": 100, "columns": int(pc.size),
             "m_local_mean": float(np.mean(m_loc)), "charge_sum_max_err": float(np.abs(pq.sum(axis=1) - 1.0).max()),
             "how": "wall time of the synchronous call, host region search and pencil assembly included"}
+
+
+def queue_scale(args):
+    """One gsk_solve of many columns through the device work queue (the
+    persistent-kernel batching of the workload), once in FIFO order and once
+    in the learned longest-first order: time, column-shift solves/s, lock-step
+    outer steps and lane utilisation sum(steps) / (outer steps * W); stored
+    oracle columns of the workload are put into the set and checked."""
+    import torch
+
+    from paper_1609_08377_gb300 import gsk, scheduler
+
+    wl, sys_, eps, cols_all, eta_all = make_workload(args.workload, args.seed)
+    S = eps.size
+    z = eps.astype(np.complex128) + 1j
+    solver = gsk.from_system(sys_)
+    scheduler.install(solver, scheduler.load())
+    n = min(args.queue_cols, cols_all.size)
+    cols, eta = cols_all[:n].copy(), eta_all[:n].copy()
+    refs = [r for r in goldens(wl.name) if int(r["column"]) not in set(cols.tolist())]
+    for t, r in enumerate(refs[: n // 8]):          # stored columns replace columns at the end of the set
+        cols[n - 1 - t], eta[n - 1 - t] = int(r["column"]), float(r["eta"])
+    W = args.batch_w or 64
+    off = solver.pattern_offsets(cols)
+    G = torch.empty(int(off[-1]) * S, dtype=torch.complex128, device="cuda")
+    res = {}
+    for sched in ("fifo", "learned"):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        it, st, _ = solver.solve(z, cols, G, eta=eta, precision=args.precision, tol=1e-8, batch_w=W, sched=sched)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        stt = solver.last_stats()
+        outer = int(stt["outer_steps"])
+        res[sched] = {"seconds": sec, "value": n * S / sec, "unit": UNIT, "outer_steps": outer,
+                      "lower_bound_steps": int(np.ceil(it.sum() / W)), "lane_utilisation": float(it.sum()) / (outer * W),
+                      "converged": int((st == 0).sum()), "columns": n}
+    Gh = G.view(int(off[-1]), S)
+    err = 0.0
+    for r in refs[: n // 8]:
+        t = int(np.nonzero(cols == int(r["column"]))[0][0])
+        R = np.array(r["G_re"]) + 1j * np.array(r["G_im"])
+        got = Gh[int(off[t]):int(off[t + 1]), ::int(r["shift_stride"])].cpu().numpy()
+        err = max(err, float(np.abs(got - R).max() / np.abs(R).max()))
+    print(json.dumps({"queue_scale": res, "workload": workload_config(wl, sys_, S, n, args, 1)["workload"],
+                      "W": W, "precision": args.precision, "oracle_columns": len(refs[: n // 8]),
+                      "dG_rel_max_learned": err}))
 
 
 # ---------------------------------------------------------------------------

@@ -404,9 +404,9 @@ int gsk_autotune_result(gsk_handle h, int32_t precision, int32_t* w, int32_t* ke
 
 /* Measured FMA throughput of the current device, for the roofline of the
  * ALU-bound kernels (the FP64 block products of gsk_marnoldi): every thread
- * runs 8 independent FMA chains over a grid of 8 CTAs per SM; *tflops (host)
- * receives the best of n_rep timed launches (CUDA events on stream, after one
- * untimed launch) in TFLOP/s, 2 flops per FMA. precision: GSK_FP64 or
+ * runs 8 or 16 independent FMA chains over a grid of 8 CTAs per SM; *tflops
+ * (host) receives the best of 2 * n_rep timed launches (CUDA events on
+ * stream, after one untimed launch) in TFLOP/s, 2 flops per FMA. precision: GSK_FP64 or
  * GSK_MIXED (FP32). Allocates a small device buffer for the chains' results.
  * Synchronous. The paper has no counterpart: it is a measurement tool. */
 int gsk_alu_peak(int32_t precision, int32_t n_rep, double* tflops, void* stream);
