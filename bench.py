@@ -651,9 +651,15 @@ def queue_scale(args):
     scheduler.install(solver, scheduler.load())
     n = min(args.queue_cols, cols_all.size)
     cols, eta = cols_all[:n].copy(), eta_all[:n].copy()
-    refs = [r for r in goldens(wl.name) if int(r["column"]) not in set(cols.tolist())]
-    for t, r in enumerate(refs[: n // 8]):          # stored columns replace columns at the end of the set
-        cols[n - 1 - t], eta[n - 1 - t] = int(r["column"]), float(r["eta"])
+    refs = goldens(wl.name)[: n // 8]
+    k = 0
+    for r in refs:          # stored columns: checked where they are in the set, else put in at its end
+        hit = np.nonzero(cols == int(r["column"]))[0]
+        if hit.size:
+            eta[hit[0]] = float(r["eta"])
+        else:
+            cols[n - 1 - k], eta[n - 1 - k] = int(r["column"]), float(r["eta"])
+            k += 1
     W = args.batch_w or 64
     off = solver.pattern_offsets(cols)
     G = torch.empty(int(off[-1]) * S, dtype=torch.complex128, device="cuda")
@@ -673,13 +679,16 @@ def queue_scale(args):
                       "converged": int((st == 0).sum()), "columns": n}
     Gh = G.view(int(off[-1]), S)
     err = 0.0
-    for r in refs[: n // 8]:
+    for r in refs:
         t = int(np.nonzero(cols == int(r["column"]))[0][0])
         R = np.array(r["G_re"]) + 1j * np.array(r["G_im"])
         got = Gh[int(off[t]):int(off[t + 1]), ::int(r["shift_stride"])].cpu().numpy()
         err = max(err, float(np.abs(got - R).max() / np.abs(R).max()))
-    print(json.dumps({"queue_scale": res, "workload": workload_config(wl, sys_, S, n, args, 1)["workload"],
-                      "W": W, "precision": args.precision, "oracle_columns": len(refs[: n // 8]),
+    desc = (f"{wl.name}: {sys_.n_atoms} atoms (1/3 C 4-orbital, 2/3 H 1-orbital), M={sys_.M}, nnz={sys_.nnz}, "
+            f"{S} shifts on [-25,5] eV; the first {n} of the {wl.n_cols or sys_.M} seeded columns (eta per column "
+            f"in {{0.05,0.1,0.2}} eV) in one gsk_solve")
+    print(json.dumps({"queue_scale": res, "workload": desc,
+                      "W": W, "precision": args.precision, "oracle_columns": len(refs),
                       "dG_rel_max_learned": err}))
 
 
