@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "gsk_common.cuh"
@@ -59,28 +60,131 @@ int ensure_host_side(gsk_ctx* h) {
   return GSK_OK;
 }
 
-// Atoms within the distance of the kappa-th nearest atom to J (ascending index).
-void region_of(const gsk_ctx* h, int32_t J, int32_t kappa, const double* box, std::vector<double>& d2,
-               std::vector<double>& tmp, std::vector<int32_t>& out) {
+// Uniform grid of cells over the atoms (periodic box, or the atoms' bounding
+// box without one), about 8 atoms per cell, for the region search.
+struct CellGrid {
+  int n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, side[3] = {1, 1, 1};
+  bool periodic = false;
+  std::vector<int32_t> start, atoms;      // cell c holds atoms[start[c] .. start[c+1])
+
+  int coord(double x, int d) const {
+    double t = x - lo[d];
+    if (periodic) t -= side[d] * n[d] * floor(t / (side[d] * n[d]));
+    int k = (int)floor(t / side[d]);
+    return std::min(std::max(k, 0), n[d] - 1);
+  }
+  void build(const double* pos, int32_t N, const double* box) {
+    periodic = box != nullptr;
+    double ext[3];
+    for (int d = 0; d < 3; ++d) {
+      if (periodic) {
+        lo[d] = 0.0;
+        ext[d] = box[d];
+      } else {
+        double a = 1e300, b = -1e300;
+        for (int32_t i = 0; i < N; ++i) {
+          a = std::min(a, pos[3 * (size_t)i + d]);
+          b = std::max(b, pos[3 * (size_t)i + d]);
+        }
+        lo[d] = a;
+        ext[d] = std::max(b - a, 1e-9);
+      }
+    }
+    const double c = cbrt(ext[0] * ext[1] * ext[2] * 8.0 / std::max(N, 1));
+    for (int d = 0; d < 3; ++d) {
+      n[d] = std::max(1, std::min(1024, (int)floor(ext[d] / std::max(c, 1e-9))));
+      side[d] = ext[d] / n[d];
+    }
+    const size_t nc = (size_t)n[0] * n[1] * n[2];
+    std::vector<int32_t> cell(N);
+    start.assign(nc + 1, 0);
+    for (int32_t i = 0; i < N; ++i) {
+      const int cx = coord(pos[3 * (size_t)i], 0), cy = coord(pos[3 * (size_t)i + 1], 1),
+                cz = coord(pos[3 * (size_t)i + 2], 2);
+      cell[i] = (cz * n[1] + cy) * n[0] + cx;
+      ++start[cell[i] + 1];
+    }
+    for (size_t k = 0; k < nc; ++k) start[k + 1] += start[k];
+    atoms.assign(N, 0);
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int32_t i = 0; i < N; ++i) atoms[fill[cell[i]]++] = i;
+  }
+  // Atoms of every cell within Chebyshev cell distance S of cell (cx, cy, cz).
+  void gather(int cx, int cy, int cz, int S, std::vector<int32_t>& out) const {
+    out.clear();
+    int lo3[3], hi3[3];
+    const int cc[3] = {cx, cy, cz};
+    for (int d = 0; d < 3; ++d) {
+      if (periodic && 2 * S + 1 >= n[d]) {        // the whole dimension, each cell once
+        lo3[d] = 0;
+        hi3[d] = n[d] - 1;
+      } else if (periodic) {
+        lo3[d] = cc[d] - S;
+        hi3[d] = cc[d] + S;
+      } else {
+        lo3[d] = std::max(0, cc[d] - S);
+        hi3[d] = std::min(n[d] - 1, cc[d] + S);
+      }
+    }
+    for (int z = lo3[2]; z <= hi3[2]; ++z)
+      for (int y = lo3[1]; y <= hi3[1]; ++y)
+        for (int x = lo3[0]; x <= hi3[0]; ++x) {
+          const int wx = ((x % n[0]) + n[0]) % n[0], wy = ((y % n[1]) + n[1]) % n[1], wz = ((z % n[2]) + n[2]) % n[2];
+          const size_t k = ((size_t)wz * n[1] + wy) * n[0] + wx;
+          out.insert(out.end(), atoms.begin() + start[k], atoms.begin() + start[k + 1]);
+        }
+  }
+};
+
+// Squared (minimum-image) distance between atoms a and J.
+inline double dist2(const double* p, int32_t a, int32_t J, const double* box) {
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double x = p[3 * (size_t)a + d] - p[3 * (size_t)J + d];
+    if (box) x -= box[d] * nearbyint(x / box[d]);
+    s += x * x;
+  }
+  return s;
+}
+
+// Atoms within the distance of the kappa-th nearest atom to J (ascending
+// index), found on the cell grid: cells are gathered in growing cubes around
+// J's cell until they hold kappa atoms; the kappa-th smallest distance D among
+// those bounds the true one, so one more gather of every cell within
+// ceil(D / cell side) + 1 holds every atom of the region, and the kappa-th
+// smallest distance there is exact.
+void region_of(const gsk_ctx* h, const CellGrid& g, int32_t J, int32_t kappa, const double* box,
+               std::vector<double>& d2, std::vector<int32_t>& cand, std::vector<int32_t>& out) {
   const int32_t N = h->n_atoms;
   const double* p = h->pos_caller.data();
-  d2.resize(N);
-  for (int32_t a = 0; a < N; ++a) {
-    double s = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      double x = p[3 * (size_t)a + d] - p[3 * (size_t)J + d];
-      if (box) x -= box[d] * nearbyint(x / box[d]);
-      s += x * x;
-    }
-    d2[a] = s;
-  }
-  tmp = d2;
   const int32_t k = std::min(kappa, N);
-  std::nth_element(tmp.begin(), tmp.begin() + (k - 1), tmp.end());
-  const double cut = tmp[k - 1];
+  const int cx = g.coord(p[3 * (size_t)J], 0), cy = g.coord(p[3 * (size_t)J + 1], 1),
+            cz = g.coord(p[3 * (size_t)J + 2], 2);
+  const int max_s = std::max(g.n[0], std::max(g.n[1], g.n[2]));
+  int S = 1;
+  for (;; ++S) {
+    g.gather(cx, cy, cz, S, cand);
+    if ((int32_t)cand.size() >= k || S >= max_s) break;
+  }
+  auto kth = [&]() {
+    d2.resize(cand.size());
+    for (size_t t = 0; t < cand.size(); ++t) d2[t] = dist2(p, cand[t], J, box);
+    std::vector<double> tmp(d2);
+    std::nth_element(tmp.begin(), tmp.begin() + (k - 1), tmp.end());
+    return tmp[k - 1];
+  };
+  double cut = kth();
+  const double cmin = std::min(g.side[0], std::min(g.side[1], g.side[2]));
+  const int S2 = (int)ceil(sqrt(cut) / cmin) + 1;
+  if (S2 > S) {
+    g.gather(cx, cy, cz, std::min(S2, max_s), cand);
+    cut = kth();
+  }
   out.clear();
-  for (int32_t a = 0; a < N; ++a)
-    if (d2[a] <= cut) out.push_back(a);
+  for (size_t t = 0; t < cand.size(); ++t)
+    if (d2[t] <= cut) out.push_back(cand[t]);
+  std::sort(out.begin(), out.end());
 }
 
 }  // namespace
@@ -103,8 +207,10 @@ int gsk_marnoldi_projected(gsk_handle h, const double* box, int32_t kappa, int32
   if (rc != GSK_OK) return rc;
 
   std::vector<int32_t> glob2loc(h->M, -1);
-  std::vector<double> d2, tmp;
-  std::vector<int32_t> atoms;
+  std::vector<double> d2;
+  std::vector<int32_t> atoms, cand;
+  CellGrid grid;
+  grid.build(h->pos_caller.data(), h->n_atoms, box);
   int64_t full_off = 0;                                 // start of the batch in the full rho layout
   for (int32_t c0 = 0; c0 < n_cols; c0 += kBatch) {
     const int nb = std::min<int>(kBatch, n_cols - c0);
@@ -120,7 +226,7 @@ int gsk_marnoldi_projected(gsk_handle h, const double* box, int32_t kappa, int32
     for (int c = 0; c < nb; ++c) {
       const int32_t j = cols[c0 + c];
       const int32_t J = h->atom_of_row[j];
-      region_of(h, J, kappa, box, d2, tmp, atoms);
+      region_of(h, grid, J, kappa, box, d2, cand, atoms);
       int32_t nloc = 0;
       for (int32_t a : atoms) {
         const int32_t f = h->atom_first_row[a], cnt = h->atom_first_row[a + 1] - f;
