@@ -51,6 +51,7 @@ struct Layout {
 // direction and of B p. Each consumer warp then runs a fixed, cost-balanced
 // list of the tile's atoms out of shared memory.
 constexpr int kTileLanes = 32;         // lanes per CTA (a W-lane batch uses W / 32 CTAs per tile)
+constexpr int kTileWarps = 8;          // consumer warps of the staged kernel (atom lists per tile)
 struct TileHead {                      // one per tile, 64 bytes
   int32_t r0;                          // first own row (library order)
   int32_t n_own;                       // own rows
@@ -63,9 +64,10 @@ struct TileHead {                      // one per tile, 64 bytes
   int64_t v0;                          // first matrix value (a multiple of 4)
   int32_t nval;                        // matrix values (a multiple of 4)
   int32_t xrows;                       // shared rows of the row union
-  uint8_t wptr[16];                    // warp w runs descriptors [wptr[w], wptr[w+1]) (kWarps + 1 used)
+  uint8_t wptr[16];                    // warp w runs descriptors [wptr[w], wptr[w+1]) (kTileWarps + 1 used)
 };
 static_assert(sizeof(TileHead) == 64, "TileHead is 64 bytes");
+static_assert(kTileWarps < 16, "the warp lists of a tile fit its header");
 // Atom descriptor (int4): x = orbitals | own row in the tile << 8 | shared
 // row of the atom's first row << 16; y = 4-orbital neighbours | 1-orbital
 // neighbour entries << 16; z = first value (from the tile's first);

@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
 // union of X = r and the tile's own rows of P and Y by 16-byte asynchronous
 // copies (cp.async, 4 rows x 128 bytes per warp instruction), and the tile's
 // matrix values, local neighbour indices and atom descriptors by 1-D TMA bulk
-// copies, all completing on the stage's "full" mbarrier. kWarps consumer
+// copies, all completing on the stage's "full" mbarrier. kTileWarps consumer
 // warps run each item's fixed atom lists out of the stage -- four groups of 8
 // threads take every fourth neighbour block of an atom, the groups are
 // combined by shuffles, and group g writes own row g: p <- r + b p,
@@ -622,8 +622,8 @@ struct SpmmStagedArgs {
   RedArgs red;
 };
 
-constexpr int kProducers = 8;                                 // producer warps of the staged kernel
-constexpr int kStagedThreads = kThreads + 32 * kProducers;   // kWarps consumer warps + the producers
+constexpr int kProducers = 8;                                        // producer warps of the staged kernel
+constexpr int kStagedThreads = 32 * (kTileWarps + kProducers);      // consumer warps + producer warps
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -634,6 +634,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_add_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -704,7 +707,7 @@ struct StageLayout {
 
 __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmStagedArgs a) {
   extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ double sred[kWarps][kMaxW];
+  __shared__ double sred[kTileWarps][kMaxW];
   __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2];
   const StageLayout SL(a.t);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(&full_bar[s], 32 * kProducers + 1);   // every producer thread's copies + the bulk copies
-      mbar_init(&empty_bar[s], kWarps);
+      mbar_init(&empty_bar[s], kTileWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -724,9 +727,9 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
   const int grp = (lane >> 3);          // consumers: 4 groups of 8 threads share one atom
   const int lane0 = (lane & 7) * 4;     // 4 lanes per thread
   bool ok = true;
-  if (warp >= kWarps) {
+  if (warp >= kTileWarps) {
     // ---------------- producers ----------------
-    const int pw = warp - kWarps;         // producer warp pw copies boxes pw, pw + kProducers, ...
+    const int pw = warp - kTileWarps;         // producer warp pw copies boxes pw, pw + kProducers, ...
     int issued = 0;
     const int sub = lane >> 3, ch = (lane & 7) * 4;
     // the next item's header and this warp's first 32 boxes are loaded one
@@ -761,26 +764,44 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
       // row union of X: 4 rows x 8 chunks of 16 bytes per warp instruction; this
       // warp copies boxes pw, pw + kProducers, ... (32 of them per register load)
       float* sX = reinterpret_cast<float*>(st + SL.x);
-      const int nmine = hd.nbox > pw ? (hd.nbox - pw + kProducers - 1) / kProducers : 0;
-      for (int k0 = 0; k0 < nmine; k0 += 32) {
-        int2 mybox = box0;
-        if (k0 > 0) mybox = (k0 + lane < nmine) ? a.t.box[hd.b0 + pw + kProducers * (k0 + lane)] : make_int2(0, 0);
-        const int kn = min(32, nmine - k0);
-        for (int k = 0; k < kn; ++k) {
-          const int g0 = __shfl_sync(0xffffffffu, mybox.x, k);
-          const int code = __shfl_sync(0xffffffffu, mybox.y, k);
-          const int hgt = 1 << (code >> 16), s0 = code & 0xffff;
-          for (int r = sub; r < hgt; r += 4)
-            cp_async16(sX + (s0 + r) * kTileLanes + ch, a.X + (size_t)(g0 + r) * a.W + qlane + ch);
-        }
-      }
-      // own rows of P and Y
       float* sP = reinterpret_cast<float*>(st + SL.p);
       float* sYs = reinterpret_cast<float*>(st + SL.y);
-      for (int r = pw * 4 + sub; r < hd.n_own; r += 4 * kProducers) {
-        const size_t g = (size_t)(hd.r0 + r) * a.W + qlane + ch;
-        cp_async16(sP + r * kTileLanes + ch, a.P + g);
-        cp_async16(sYs + r * kTileLanes + ch, a.Y + g);
+      const int nmine = hd.nbox > pw ? (hd.nbox - pw + kProducers - 1) / kProducers : 0;
+      if (a.nq == 1) {
+        // 32 lanes: a piece of a row run is contiguous in X, one bulk copy per piece
+        for (int k0 = 0; k0 < nmine; k0 += 32) {
+          int2 mybox = box0;
+          if (k0 > 0) mybox = (k0 + lane < nmine) ? a.t.box[hd.b0 + pw + kProducers * (k0 + lane)] : make_int2(0, 0);
+          if (k0 + lane < nmine) {
+            const uint32_t bytes = (uint32_t)(kTileLanes * sizeof(float)) << (mybox.y >> 16);
+            mbar_add_tx(&full_bar[s], bytes);
+            bulk_copy(sX + (mybox.y & 0xffff) * kTileLanes, a.X + (size_t)mybox.x * kTileLanes, bytes, &full_bar[s]);
+          }
+        }
+        if (pw == 1 && lane < 2) {
+          const uint32_t bytes = (uint32_t)hd.n_own * kTileLanes * sizeof(float);
+          mbar_add_tx(&full_bar[s], bytes);
+          bulk_copy(lane == 0 ? sP : sYs, (lane == 0 ? a.P : a.Y) + (size_t)hd.r0 * kTileLanes, bytes, &full_bar[s]);
+        }
+      } else {
+        for (int k0 = 0; k0 < nmine; k0 += 32) {
+          int2 mybox = box0;
+          if (k0 > 0) mybox = (k0 + lane < nmine) ? a.t.box[hd.b0 + pw + kProducers * (k0 + lane)] : make_int2(0, 0);
+          const int kn = min(32, nmine - k0);
+          for (int k = 0; k < kn; ++k) {
+            const int g0 = __shfl_sync(0xffffffffu, mybox.x, k);
+            const int code = __shfl_sync(0xffffffffu, mybox.y, k);
+            const int hgt = 1 << (code >> 16), s0 = code & 0xffff;
+            for (int r = sub; r < hgt; r += 4)
+              cp_async16(sX + (s0 + r) * kTileLanes + ch, a.X + (size_t)(g0 + r) * a.W + qlane + ch);
+          }
+        }
+        // own rows of P and Y
+        for (int r = pw * 4 + sub; r < hd.n_own; r += 4 * kProducers) {
+          const size_t g = (size_t)(hd.r0 + r) * a.W + qlane + ch;
+          cp_async16(sP + r * kTileLanes + ch, a.P + g);
+          cp_async16(sYs + r * kTileLanes + ch, a.Y + g);
+        }
       }
       cp_async_arrive(&full_bar[s]);
       issued = j + 1;
@@ -920,7 +941,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
     dot[i] += __shfl_xor_sync(0xffffffffu, dot[i], 8);
     dot[i] += __shfl_xor_sync(0xffffffffu, dot[i], 16);
   }
-  if (warp < kWarps && grp == 0) {
+  if (warp < kTileWarps && grp == 0) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) sred[warp][lane0 + i] = (double)dot[i];
   }
@@ -928,7 +949,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
   double sum = 0.0;
   if (threadIdx.x < a.W && threadIdx.x / kTileLanes == q) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) sum += sred[w][threadIdx.x % kTileLanes];
+    for (int w = 0; w < kTileWarps; ++w) sum += sred[w][threadIdx.x % kTileLanes];
   }
   __syncthreads();
   cta_sums_commit(sum, a.red, sred);

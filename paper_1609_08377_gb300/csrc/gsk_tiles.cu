@@ -134,17 +134,17 @@ int plan_tiles(const std::vector<int32_t>& roff, const std::vector<int8_t>& orb,
                        [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
                          return x.first > y.first;
                        });
-      double load[kWarps] = {0};
-      std::vector<int32_t> lists[kWarps];
+      double load[kTileWarps] = {0};
+      std::vector<int32_t> lists[kTileWarps];
       for (const auto& c : cost) {
         int w = 0;
-        for (int k = 1; k < kWarps; ++k)
+        for (int k = 1; k < kTileWarps; ++k)
           if (load[k] < load[w]) w = k;
         load[w] += c.first;
         lists[w].push_back(c.second);
       }
       int nd = 0;
-      for (int w = 0; w < kWarps; ++w) {
+      for (int w = 0; w < kTileWarps; ++w) {
         std::sort(lists[w].begin(), lists[w].end());
         hd.wptr[w] = (uint8_t)nd;
         for (int32_t I : lists[w]) {
@@ -160,7 +160,7 @@ int plan_tiles(const std::vector<int32_t>& roff, const std::vector<int8_t>& orb,
           ++nd;
         }
       }
-      hd.wptr[kWarps] = (uint8_t)nd;
+      hd.wptr[kTileWarps] = (uint8_t)nd;
     }
     for (size_t k = 0; k < uni.size(); ++k) srow[uni[k]] = -1;
     P.head.push_back(hd);
