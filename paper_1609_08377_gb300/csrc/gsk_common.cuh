@@ -43,15 +43,16 @@ struct Layout {
   const int32_t* warp_atoms;     // n_ctas * kWarps + 1: atoms [warp_atoms[w], warp_atoms[w+1]) of warp w
 };
 
-// Tiles of the staged SpMM (k_spmm_tiled). Atoms are cut, in library order,
+// Tiles of the staged SpMM (k_spmm_staged). Atoms are cut, in library order,
 // into tiles of consecutive atoms; a tile's CTA copies into shared memory the
 // rows of every neighbour atom of the tile (its row union, contiguous row
-// runs cut into pieces of 8, 4, 2 or 1 rows), the tile's matrix values, local
+// runs cut into pieces of at most kPieceRows rows), the tile's matrix values, local
 // neighbour indices and atom descriptors, and the tile's own rows of the CG
 // direction and of B p. Each consumer warp then runs a fixed, cost-balanced
 // list of the tile's atoms out of shared memory.
 constexpr int kTileLanes = 32;         // lanes per CTA (a W-lane batch uses W / 32 CTAs per tile)
 constexpr int kTileWarps = 8;          // consumer warps of the staged kernel (atom lists per tile)
+constexpr int kPieceRows = 16;         // longest row-run piece (one copy of up to 2 KB per 32 lanes)
 struct TileHead {                      // one per tile, 64 bytes
   int32_t r0;                          // first own row (library order)
   int32_t n_own;                       // own rows
@@ -80,7 +81,7 @@ struct TileArgs {
   int32_t l_cap;                 // shared local indices (int16)
   int32_t d_cap;                 // shared atom descriptors
   const TileHead* head;          // n_tiles
-  const int2* box;               // row-run pieces: (first global row, first shared row | log2(rows) << 16)
+  const int2* box;               // row-run pieces: (first global row, first shared row | rows << 16)
   const int16_t* loc;            // shared row of each neighbour entry's first row, tile by tile
   const int4* desc;              // atom descriptors, tile by tile, in warp order
   const int32_t* order;          // library atom of each descriptor

@@ -597,10 +597,12 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const SpmmArgs<TV, TX, TY> a)
 // a W-lane batch runs W/32 lane quarters per tile, and gridDim.x is a
 // multiple of W/32, so a CTA keeps one quarter q = blockIdx.x % (W/32).
 // kProducers producer warps fill two shared-memory stages in turn: the row
-// union of X = r and the tile's own rows of P and Y by 16-byte asynchronous
-// copies (cp.async, 4 rows x 128 bytes per warp instruction), and the tile's
-// matrix values, local neighbour indices and atom descriptors by 1-D TMA bulk
-// copies, all completing on the stage's "full" mbarrier. kTileWarps consumer
+// union of X = r and the tile's own rows of P and Y -- with 32 lanes (a row
+// run is then contiguous in memory) by one 1-D TMA bulk copy per row-run
+// piece and per own-row range, with 64 or 128 lanes by 16-byte asynchronous
+// copies (cp.async, 4 rows x 128 bytes per warp instruction) -- and the
+// tile's matrix values, local neighbour indices and atom descriptors by 1-D
+// TMA bulk copies, all completing on the stage's "full" mbarrier. kTileWarps consumer
 // warps run each item's fixed atom lists out of the stage -- four groups of 8
 // threads take every fourth neighbour block of an atom, the groups are
 // combined by shuffles, and group g writes own row g: p <- r + b p,
@@ -773,7 +775,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
           int2 mybox = box0;
           if (k0 > 0) mybox = (k0 + lane < nmine) ? a.t.box[hd.b0 + pw + kProducers * (k0 + lane)] : make_int2(0, 0);
           if (k0 + lane < nmine) {
-            const uint32_t bytes = (uint32_t)(kTileLanes * sizeof(float)) << (mybox.y >> 16);
+            const uint32_t bytes = (uint32_t)(kTileLanes * sizeof(float)) * (uint32_t)(mybox.y >> 16);
             mbar_add_tx(&full_bar[s], bytes);
             bulk_copy(sX + (mybox.y & 0xffff) * kTileLanes, a.X + (size_t)mybox.x * kTileLanes, bytes, &full_bar[s]);
           }
@@ -791,7 +793,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
           for (int k = 0; k < kn; ++k) {
             const int g0 = __shfl_sync(0xffffffffu, mybox.x, k);
             const int code = __shfl_sync(0xffffffffu, mybox.y, k);
-            const int hgt = 1 << (code >> 16), s0 = code & 0xffff;
+            const int hgt = code >> 16, s0 = code & 0xffff;
             for (int r = sub; r < hgt; r += 4)
               cp_async16(sX + (s0 + r) * kTileLanes + ch, a.X + (size_t)(g0 + r) * a.W + qlane + ch);
           }

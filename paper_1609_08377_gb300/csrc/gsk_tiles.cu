@@ -103,14 +103,9 @@ int plan_tiles(const std::vector<int32_t>& roff, const std::vector<int8_t>& orb,
       const int r0 = roff[uni[a]];
       const int n = roff[uni[b - 1] + 1] - r0;
       for (size_t k = a; k < b; ++k) srow[uni[k]] = srow_next + (roff[uni[k]] - r0);
-      // boxes of 8, 4, 2 and 1 rows tile the run exactly
-      int off = 0;
-      for (; n - off >= 8; off += 8) P.box.push_back(make_int2(r0 + off, (srow_next + off) | (3 << 16)));
-      for (int hc = 2; hc >= 0; --hc)
-        if ((n - off) & (1 << hc)) {
-          P.box.push_back(make_int2(r0 + off, (srow_next + off) | (hc << 16)));
-          off += 1 << hc;
-        }
+      // pieces of at most kPieceRows rows tile the run exactly
+      for (int off = 0; off < n; off += kPieceRows)
+        P.box.push_back(make_int2(r0 + off, (srow_next + off) | (std::min(kPieceRows, n - off) << 16)));
       srow_next += n;
       a = b;
     }

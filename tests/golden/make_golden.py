@@ -11,6 +11,17 @@ shift_stride-th shift, from a run to a 1e-10 residual. Usage:
     python tests/golden/make_golden.py ch100k --batch 0.2:24 0.1:24
         # a batch: the first 24 columns of the seeded subset with eta = 0.2
         # and the first 24 with eta = 0.1 that have no stored file yet
+    python tests/golden/make_golden.py ch1m --steps 16 16
+        # the first 16 columns of the seeded subset, stopped after exactly 16
+        # Lanczos steps (files <workload>_steps<n>_col<j>.json)
+
+The --steps mode is for pencils where a converged oracle column takes hours:
+after n steps both the oracle and the solver return the Galerkin solution of
+the n-step Krylov subspace, x_n(z) = Q_n (z - T_n)^{-1} beta_0 e_1 (Sec.
+III-B). The file also stores, per column, how far that G moves when the
+oracle's inner CG stops at a relative residual of 1e-10 instead of 1e-14
+("spread_bsolve_1e-10"): the rounding sensitivity of the unconverged
+iterate, measured, from which a test sets its tolerance.
 
 Columns are taken in the order of the workload's seeded column subset
 (synthetic.column_subset), each with its seeded damping
@@ -34,6 +45,9 @@ SHIFT_STRIDE = 8
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCE_ONE = ("oracle/krylov.py lanczos_column (naive FP64 B-Lanczos, CG inner solves to 1e-14), "
               "tol 1e-10; Sec. III-B of arXiv:1609.08377 (generalized shifted equations)")
+SOURCE_STEPS = ("oracle/krylov.py lanczos_batch (naive FP64 B-Lanczos over a batch of columns, C loops in "
+                "oracle/o3_batch.c, CG inner solves to 1e-14) stopped after a fixed number of steps n: "
+                "G_n = Q_n (z - T_n)^-1 beta_0 e_1; Sec. III-B of arXiv:1609.08377")
 SOURCE_BATCH = ("oracle/krylov.py lanczos_batch (naive FP64 B-Lanczos over a batch of columns, C loops in "
                 "oracle/o3_batch.c, CG inner solves to 1e-14), tol 1e-10; Sec. III-B of arXiv:1609.08377 "
                 "(generalized shifted equations)")
@@ -119,9 +133,50 @@ def batch(name, classes):
                          milestones=(1e-8,), progress=progress, on_done=done)
 
 
+def fixed_steps(name, n, k):
+    """The first k columns of the seeded subset after exactly n oracle steps."""
+    wl = syn.WORKLOADS[name]
+    t0 = time.time()
+    s = syn.make_system(wl.n_atoms, wl.c_fraction, 0)
+    n_cols = wl.n_cols if wl.n_cols is not None else s.M
+    cols = syn.column_subset(s.M, n_cols, 0)
+    eta = syn.eta_per_column(cols.size, 0) if wl.eta is None else np.full(cols.size, wl.eta)
+    js = [int(j) for j in cols[:k]]
+    es = [float(e) for e in eta[:k]]
+    eps = syn.energy_grid(wl.n_shifts)
+    z = [syn.shifts(eps, e) for e in es]
+    print(name, "pencil", s.M, "rows", s.A.nnz, "nnz", f"{time.time() - t0:.0f} s; columns", list(zip(js, es)),
+          "threads", krylov.set_threads(0), flush=True)
+
+    def run(btol):
+        t1 = time.time()
+        r = krylov.lanczos_batch(s.A, s.B, js, z, tol=0.0, max_iter=n, check_every=n, bsolve_tol=btol)
+        print(f"{n} steps, inner CG to {btol:g}: {time.time() - t1:.0f} s", flush=True)
+        return r, time.time() - t1
+
+    ref, sec = run(1e-14)
+    loose, _ = run(1e-10)
+    for c, j in enumerate(js):
+        R = ref[c].G[:, ::SHIFT_STRIDE]
+        L = loose[c].G[:, ::SHIFT_STRIDE]
+        spread = float(np.abs(R - L).max() / np.abs(R).max())
+        out = {
+            "source": SOURCE_STEPS, "workload": name, "seed": 0, "column": j, "eta": es[c],
+            "n_shifts": int(wl.n_shifts), "shift_stride": SHIFT_STRIDE, "steps": int(n),
+            "spread_bsolve_1e-10": spread, "seconds": sec,
+            "G_re": [[float(v) for v in row] for row in R.real],
+            "G_im": [[float(v) for v in row] for row in R.imag],
+        }
+        with open(os.path.join(HERE, f"{name}_steps{n}_col{j}.json"), "w") as f:
+            json.dump(out, f)
+        print(name, j, es[c], "spread", f"{spread:.2e}", flush=True)
+
+
 def main():
     name = sys.argv[1]
-    if sys.argv[2] == "--batch":
+    if sys.argv[2] == "--steps":
+        fixed_steps(name, int(sys.argv[3]), int(sys.argv[4]))
+    elif sys.argv[2] == "--batch":
         classes = [(float(a), int(b)) for a, b in (x.split(":") for x in sys.argv[3:])]
         batch(name, classes)
     else:

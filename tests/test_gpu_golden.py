@@ -12,6 +12,9 @@ step count must agree with the oracle's step count at the 1e-8 level (the
 oracle checks the residual every 10 steps). At 10^6 atoms G_ij from column j
 also equals G_ji from column i for a neighbour pair (G(z)^T = G(z) for
 symmetric A and B), the property checked where no stored columns exist.
+Where a converged oracle column is out of reach (10^6 atoms), stored oracle
+columns after a fixed number n of Lanczos steps are compared with the
+solver stopped after the same n steps (tests/golden/*_steps*_col*.json).
 """
 
 import glob
@@ -141,4 +144,62 @@ def test_1m_symmetry_and_stored_columns():
     g_ij = Gh[off[c_j] + int(np.nonzero(rows_j == i)[0][0])]     # row i of column j
     g_ji = Gh[off[c_i] + int(np.nonzero(rows_i == j)[0][0])]     # row j of column i
     assert np.abs(g_ij - g_ji).max() <= 1e-8 * np.abs(Gh).max()
+    solver.close()
+
+
+def _steps_golden(name):
+    return [json.load(open(p))
+            for p in sorted(glob.glob(os.path.join(HERE, "golden", f"{name}_steps*_col*.json")))]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_df"])
+def test_1m_fixed_steps_against_oracle(prec):
+    """The 1,000,000-atom pencil against the oracle where a converged oracle
+    column is out of reach: after exactly n Lanczos steps both sides return
+    the Galerkin solution of the n-step Krylov subspace, x_n(z) = Q_n (z -
+    T_n)^{-1} beta_0 e_1 (Sec. III-B), on 16 seeded columns of all three
+    damping classes. An unconverged iterate carries the rounding of the inner
+    B-solves, amplified near the early Ritz values: each stored column gives
+    how far the oracle's own G_n moves when its inner CG stops at 1e-10
+    instead of 1e-14 (the spread; 9e-10 to 2.4e-4 over these columns, largest
+    at eta = 0.05). The change is first order in the inner-solve error, so the
+    FP64 solve (inner CG to 1e-14, 1e-4 of the probe's error) must agree to
+    1e-3 of the spread (at least 1e-10), and the double-float mode (an FP32
+    pass to 3e-6 and one refinement pass, about 1e-11) to twice the spread
+    (at least 1e-9). This checks the solver at 10^6 atoms against the oracle;
+    the converged 1e-8 check of the smaller workloads is not reachable here."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    refs = _steps_golden("ch1m")
+    if not refs:
+        pytest.skip("no stored fixed-step oracle columns for ch1m")
+    from paper_1609_08377_gb300 import gsk
+
+    n = int(refs[0]["steps"])
+    assert all(int(r["steps"]) == n for r in refs)
+    wl = syn.WORKLOADS["ch1m"]
+    s = _system("ch1m")
+    solver = gsk.from_system(s)
+    cols = np.array([int(r["column"]) for r in refs], dtype=np.int32)
+    eta = np.array([float(r["eta"]) for r in refs])
+    eps = syn.energy_grid(wl.n_shifts)
+    z = eps.astype(np.complex128) + 1j
+    off = solver.pattern_offsets(cols)
+    G = torch.zeros(int(off[-1]) * wl.n_shifts, dtype=torch.complex128, device="cuda")
+    kw = dict(inner_tol=1e-14) if prec == "fp64" else {}
+    it, st, _ = solver.solve(z, cols, G, eta=eta, precision=prec, tol=1e-30, max_iter=n, batch_w=32,
+                             sched="fifo", **kw)
+    torch.cuda.synchronize()
+    assert (it == n).all() and (st == gsk.GSK_NOT_CONVERGED).all()
+    Gh = G.cpu().numpy().reshape(int(off[-1]), wl.n_shifts)
+    errs = []
+    for c, r in enumerate(refs):
+        R = np.array(r["G_re"]) + 1j * np.array(r["G_im"])
+        got = Gh[off[c]:off[c + 1], ::r["shift_stride"]]
+        err = np.abs(got - R).max() / np.abs(R).max()
+        spread = float(r["spread_bsolve_1e-10"])
+        bar = max(1e-10, 1e-3 * spread) if prec == "fp64" else max(1e-9, 2.0 * spread)
+        errs.append((r["column"], err, bar))
+        assert err <= bar, (r["column"], err, bar)
+    print(prec, "worst |dG|/max|G| after", n, "steps:", max(e for _, e, _ in errs))
     solver.close()
