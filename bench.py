@@ -539,7 +539,7 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 dense FP64 (profiling recipe); gsk_alu_peak'
 # inner-CG product from one ncu capture per (workload, kernel, value bytes, W),
 # with the profiles/ summary that records it
 _NCU_TRAFFIC = {
-    ("ch100k", "staged", 4, 32): (212.70e6, "profiles/spmm_staged_ch100k_w32.md (ncu --set full, one launch)"),
+    ("ch100k", "staged", 4, 32): (211.58e6, "profiles/spmm_staged_ch100k_w32.md (ncu --set full, one launch of the 12 + 4 warp kernel)"),
 }
 
 

@@ -57,7 +57,7 @@ extern "C" {
                                 residuals, Lanczos vectors, inner products) in double-float
                                 arithmetic: pairs of FP32 numbers, 48-bit significand */
 
-#define GSK_SPMM_AUTO 0      /* inner-CG products: the autotuner's pick, else staged up to 64 lanes (default) */
+#define GSK_SPMM_AUTO 0      /* inner-CG products: the autotuner's pick, else staged at 32 lanes (default) */
 #define GSK_SPMM_GATHER 1    /* every product by the per-atom gather kernel */
 #define GSK_SPMM_STAGED 2    /* FP32 inner-CG products: tile rows staged in shared memory (mixed modes) */
 

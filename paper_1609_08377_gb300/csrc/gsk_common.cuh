@@ -51,7 +51,7 @@ struct Layout {
 // direction and of B p. Each consumer warp then runs a fixed, cost-balanced
 // list of the tile's atoms out of shared memory.
 constexpr int kTileLanes = 32;         // lanes per CTA (a W-lane batch uses W / 32 CTAs per tile)
-constexpr int kTileWarps = 8;          // consumer warps of the staged kernel (atom lists per tile)
+constexpr int kTileWarps = 12;         // consumer warps of the staged kernel (atom lists per tile)
 constexpr int kPieceRows = 16;         // longest row-run piece (one copy of up to 2 KB per 32 lanes)
 struct TileHead {                      // one per tile, 64 bytes
   int32_t r0;                          // first own row (library order)

@@ -624,7 +624,7 @@ struct SpmmStagedArgs {
   RedArgs red;
 };
 
-constexpr int kProducers = 8;                                        // producer warps of the staged kernel
+constexpr int kProducers = 4;                                        // producer warps of the staged kernel
 constexpr int kStagedThreads = 32 * (kTileWarps + kProducers);      // consumer warps + producer warps
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -2006,10 +2006,10 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
     }
     if (kind == GSK_SPMM_AUTO) {
       // the autotuner's pick for this lane width, else the measured rule: the
-      // staged kernel up to 64 lanes, the gather kernel at 128
+      // staged kernel at 32 lanes, the gather kernel at 64 and 128
       const int wi = W == 32 ? 0 : W == 64 ? 1 : 2;
       kind = h->tuned_kernel[opt.precision][wi] != 0 ? h->tuned_kernel[opt.precision][wi]
-                                                     : (W <= 64 ? GSK_SPMM_STAGED : GSK_SPMM_GATHER);
+                                                     : (W == 32 ? GSK_SPMM_STAGED : GSK_SPMM_GATHER);
     }
     if (kind == GSK_SPMM_STAGED) {
       const int nq = W / kTileLanes;

@@ -116,6 +116,16 @@ def _ptr(a) -> int:
     return a.ctypes.data
 
 
+def _per_column(v, n: int) -> np.ndarray:
+    """A per-column FP64 array of n entries (a scalar is repeated; another length is refused)."""
+    a = np.asarray(v, dtype=np.float64)
+    if a.ndim == 0:
+        a = np.full(n, float(a))
+    if a.shape != (n,):
+        raise ValueError(f"expected {n} per-column values, got shape {a.shape}")
+    return np.ascontiguousarray(a)
+
+
 def default_options(**kw) -> Options:
     o = Options()
     _lib.gsk_default_options(C.byref(o))
@@ -187,7 +197,7 @@ class Solver:
     def features(self, cols, eta, feat) -> None:
         """Scheduler features of the columns into feat (device tensor, n x 16 float32)."""
         cols = np.ascontiguousarray(cols, dtype=np.int32)
-        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        eta = _per_column(eta, cols.size)
         _check(_lib.gsk_features(self._h, cols.size, _ptr(cols), _ptr(eta), _ptr(feat), None), "gsk_features")
 
     def set_sched_model(self, params, norm) -> None:
@@ -219,7 +229,7 @@ class Solver:
         z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
         zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).ravel())
         cols = np.ascontiguousarray(cols, dtype=np.int32)
-        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        e = None if eta is None else _per_column(eta, cols.size)
         opt = options if options is not None else default_options(**kw)
         n = cols.size
         iters = np.empty(n, dtype=np.int32)
@@ -235,7 +245,7 @@ class Solver:
         z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
         zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).ravel())
         cols = np.ascontiguousarray(cols, dtype=np.int32)
-        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        e = None if eta is None else _per_column(eta, cols.size)
         opt = default_options(**kw)
         w = C.c_int32()
         _check(_lib.gsk_autotune(self._h, z.size, _ptr(zz), _ptr(e), cols.size, _ptr(cols), C.byref(opt),

@@ -128,3 +128,19 @@ def test_binding_signatures_match_header(libgsk):
         assert len(f.argtypes) == proto_n, (name, len(f.argtypes), proto_n)
         checked += 1
     assert checked >= 25
+
+
+def test_per_column_values_are_marshalled_to_n_entries(libgsk):
+    """Per-column damping passed to gsk_solve / gsk_autotune / gsk_features
+    reaches the C side as exactly n_cols doubles: a scalar is repeated, an
+    array of another length is refused on the host (the C side reads n_cols
+    entries from the pointer)."""
+    g = libgsk
+    a = g._per_column(0.2, 3)
+    assert a.dtype == np.float64 and a.shape == (3,) and (a == 0.2).all() and a.flags.c_contiguous
+    b = g._per_column(np.array([0.05, 0.1, 0.2], dtype=np.float32), 3)
+    assert b.dtype == np.float64 and np.allclose(b, [0.05, 0.1, 0.2])
+    with pytest.raises(ValueError):
+        g._per_column(np.array([0.1, 0.2]), 3)
+    with pytest.raises(ValueError):
+        g._per_column(np.zeros((3, 1)), 3)

@@ -108,6 +108,19 @@ def test_solve_staged_matches_lu(gsk, systems, kern, prec, W):
     solver.close()
 
 
+def test_default_kernel_by_lane_width(gsk, systems):
+    """Without an autotuner pick, the mixed modes run the staged product at 32
+    lanes and the gather product at 64 and 128 (the measured rule)."""
+    s = systems["ch1k"]
+    solver = gsk.from_system(s)
+    z = syn.energy_grid(8).astype(np.complex128) + 1j
+    cols = np.arange(4, dtype=np.int32)
+    for W, kind in ((32, gsk.GSK_SPMM_STAGED), (64, gsk.GSK_SPMM_GATHER), (128, gsk.GSK_SPMM_GATHER)):
+        _solve(gsk, solver, z, cols, eta=np.full(cols.size, 0.2), precision="mixed_df", tol=1e-8, batch_w=W)
+        assert solver.last_stats()["spmm_kernel"] == kind, W
+    solver.close()
+
+
 def test_solve_staged_ch1k_per_column_eta(gsk, systems):
     s = systems["ch1k"]
     eps = syn.energy_grid(32)
@@ -115,8 +128,9 @@ def test_solve_staged_ch1k_per_column_eta(gsk, systems):
     eta = syn.eta_per_column(cols.size, 5)
     solver = gsk.from_system(s)
     z = eps.astype(np.complex128) + 1j
-    G, it, st = _solve(gsk, solver, z, cols, eta=eta, precision="mixed_df", tol=1e-10, batch_w=64)
-    assert solver.last_stats()["spmm_kernel"] == gsk.GSK_SPMM_STAGED    # the default up to 64 lanes
+    G, it, st = _solve(gsk, solver, z, cols, eta=eta, precision="mixed_df", tol=1e-10, batch_w=64,
+                       spmm_kernel="staged")
+    assert solver.last_stats()["spmm_kernel"] == gsk.GSK_SPMM_STAGED
     assert (st == gsk.GSK_CONVERGED).all()
     off = solver.pattern_offsets(cols)
     worst = 0.0
