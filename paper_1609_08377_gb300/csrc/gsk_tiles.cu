@@ -138,11 +138,20 @@ int plan_tiles(const std::vector<int32_t>& roff, const std::vector<int8_t>& orb,
         load[w] += c.first;
         lists[w].push_back(c.second);
       }
+      // warp slots take the lists heaviest first on even tiles and lightest
+      // first on odd ones: a warp runs at most one tile ahead of the slowest
+      // (two stages), so alternating evens out each warp's load over a pair of
+      // tiles instead of giving the same warps the 4-orbital atoms every time
+      int order[kTileWarps];
+      for (int w = 0; w < kTileWarps; ++w) order[w] = w;
+      std::stable_sort(order, order + kTileWarps, [&](int x, int y) { return load[x] > load[y]; });
+      if (P.head.size() & 1) std::reverse(order, order + kTileWarps);
       int nd = 0;
-      for (int w = 0; w < kTileWarps; ++w) {
-        std::sort(lists[w].begin(), lists[w].end());
-        hd.wptr[w] = (uint8_t)nd;
-        for (int32_t I : lists[w]) {
+      for (int slot = 0; slot < kTileWarps; ++slot) {
+        std::vector<int32_t>& lst = lists[order[slot]];
+        std::sort(lst.begin(), lst.end());
+        hd.wptr[slot] = (uint8_t)nd;
+        for (int32_t I : lst) {
           const int n4 = nbr_mid[I] - nbr_ptr[I];
           const int n1 = nbr_ptr[I + 1] - nbr_mid[I];
           int4 d;
