@@ -24,6 +24,31 @@
  *  - Indices are 0-based and refer to the caller's original ordering.
  *  - Calls on one handle are not thread safe; different handles are
  *    independent.
+ *
+ * Bounds-checked build: libgsk compiled with -DGSK_DEBUG (build.py's
+ * debug build, libgsk_debug.so) has the same entry points. Its solve kernels
+ * test every block-layout, tile and work-queue index before they use it; a
+ * failed test records the first offence and skips the access (or sends it to
+ * a valid row), so no kernel faults or traps on a bad index. gsk_solve and
+ * gsk_spmm then return GSK_EBOUNDS and gsk_stats.debug_code / debug_index
+ * name the check and the index (results are then unspecified); gsk_spmm
+ * waits for its kernels in that build. The check codes:
+ *    1  atom index, orbital count or own rows of an atom (gather products)
+ *    2  neighbour-entry range or value range of an atom (gather products)
+ *    3  neighbour row outside the rows of X (gather products)
+ *   10  tile header: a copy outside the tile arrays, the values or the stage
+ *       buffers, or a misaligned bulk copy (staged product, producers)
+ *   11  row-run piece outside X or the stage's row buffer (producers)
+ *   12  a warp's atom list outside the tile's descriptors (consumers)
+ *   13  atom descriptor: own rows, values or neighbour indices outside the
+ *       stage (consumers)
+ *   14  shared row of a neighbour outside the stage's row buffer (consumers)
+ *   20  work-queue entry that is not a job index
+ *   21  a lane's job index outside the solve's columns
+ *   22  row of e_j outside [0, M)
+ *   23  pattern size of a column above the per-lane buffers
+ *   24  pattern row outside [0, M) (shift recurrences)
+ * The normal build compiles every check away.
  */
 #ifndef GSK_H
 #define GSK_H
@@ -43,6 +68,7 @@ extern "C" {
 #define GSK_ECUDA (-4)      /* a CUDA runtime call failed */
 #define GSK_ETIMEOUT (-5)   /* a bounded device wait gave up */
 #define GSK_ENOTSUP (-6)    /* option combination not supported (e.g. FP64 with 128 lanes) */
+#define GSK_EBOUNDS (-7)    /* bounds-checked build only: an index check failed (see gsk_stats) */
 
 /* ----- per-column status codes (status[] of gsk_solve) -------------------- */
 #define GSK_CONVERGED 0      /* every shift reached the residual tolerance */
@@ -419,6 +445,9 @@ typedef struct {
   int32_t batch_w;           /* lanes used */
   int32_t used_graph;        /* 1 when the solve ran as one CUDA graph */
   int32_t spmm_kernel;       /* GSK_SPMM_GATHER or GSK_SPMM_STAGED: kernel of the inner-CG products */
+  int32_t debug_code;        /* bounds-checked build: first failed index check of the last gsk_solve or
+                                gsk_spmm (a code listed at the top of this file), 0 = none; always 0 otherwise */
+  int64_t debug_index;       /* the index that failed it */
 } gsk_stats;
 
 /* Copy the counters of the last gsk_solve into *out (host). */
@@ -426,6 +455,14 @@ int gsk_last_stats(gsk_handle h, gsk_stats* out);
 
 /* Human-readable text for a GSK_* code. */
 const char* gsk_strerror(int code);
+
+/* Bounds-checked build: runs one kernel whose index check fails on purpose
+ * (it guards no memory access) and reads the record back: *code (host) = 99,
+ * *index (host) = 12345678901 when the recording path works; the record is
+ * cleared again. Synchronous, on the legacy default stream, no handle. The
+ * normal build returns GSK_ENOTSUP with *code = *index = 0. A test utility
+ * of the library; the paper has no counterpart. */
+int gsk_debug_selftest(int32_t* code, int64_t* index);
 
 #ifdef __cplusplus
 }

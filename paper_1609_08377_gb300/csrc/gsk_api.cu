@@ -210,6 +210,7 @@ const char* gsk_strerror(int code) {
     case GSK_ECUDA: return "CUDA runtime error";
     case GSK_ETIMEOUT: return "bounded device wait gave up";
     case GSK_ENOTSUP: return "option combination not supported";
+    case GSK_EBOUNDS: return "bounds-checked build: an index check failed (see gsk_stats.debug_code)";
     default: return "unknown gsk status";
   }
 }
@@ -476,6 +477,10 @@ int gsk_create(const gsk_csr* A, const gsk_csr* B, const gsk_orbmap* map, gsk_ha
   L.nbr_mid = h->d_nbr_mid.as<int32_t>();
   L.nbr_roff = h->d_nbr_roff.as<int32_t>();
   L.val_ptr = h->d_val_ptr.as<int64_t>();
+#ifdef GSK_DEBUG
+  L.n_nbr = h->n_nbr;
+  L.n_vals = h->n_vals;
+#endif
   h->atom_perm = std::move(perm);
   h->atom_of_row = std::move(atom_of_row);
   h->orb_lib = std::move(orb);

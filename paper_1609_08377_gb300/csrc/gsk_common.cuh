@@ -41,6 +41,10 @@ struct Layout {
   const int32_t* nbr_roff;       // neighbour entries
   const int64_t* val_ptr;        // n_atoms
   const int32_t* warp_atoms;     // n_ctas * kWarps + 1: atoms [warp_atoms[w], warp_atoms[w+1]) of warp w
+#ifdef GSK_DEBUG
+  int32_t n_nbr;                 // neighbour entries (the length of nbr_roff)
+  int64_t n_vals;                // values of the block layout (the length of each value copy)
+#endif
 };
 
 // Tiles of the staged SpMM (k_spmm_staged). Atoms are cut, in library order,
@@ -85,6 +89,10 @@ struct TileArgs {
   const int16_t* loc;            // shared row of each neighbour entry's first row, tile by tile
   const int4* desc;              // atom descriptors, tile by tile, in warp order
   const int32_t* order;          // library atom of each descriptor
+#ifdef GSK_DEBUG
+  int32_t n_box, n_loc, n_desc;  // lengths of box, loc and desc
+  int64_t n_vals;                // length of the value copy the tiles index
+#endif
 };
 
 // Lane states of the batched solver.

@@ -42,6 +42,29 @@
 namespace gsk {
 
 // ===========================================================================
+// Bounds-checked build (-DGSK_DEBUG)
+// ===========================================================================
+// The solve's kernels test the block-layout, tile and work-queue indices
+// before they use them. A failed test records the first offence -- a code
+// naming the check (include/gsk.h lists them) and the offending index -- in
+// g_dbg, and the access is skipped or sent to a valid row, so the kernel ends
+// normally and gsk_solve / gsk_spmm return GSK_EBOUNDS. No check traps. In the
+// normal build every check is the constant true and compiles away.
+#ifdef GSK_DEBUG
+__device__ int g_dbg[4];       // first code, index (low, high word), failed checks
+__device__ __noinline__ void dbg_fail(int code, long long idx) {
+  if (atomicCAS(&g_dbg[0], 0, code) == 0) {
+    g_dbg[1] = (int)(idx & 0xffffffffLL);
+    g_dbg[2] = (int)(idx >> 32);
+  }
+  atomicAdd(&g_dbg[3], 1);
+}
+#define GSK_IDX_OK(cond, code, idx) ((cond) ? true : (::gsk::dbg_fail((code), (long long)(idx)), false))
+#else
+#define GSK_IDX_OK(cond, code, idx) true
+#endif
+
+// ===========================================================================
 // Finalisation of per-lane sums (runs in the last CTA of a reducing kernel)
 // ===========================================================================
 __device__ void finalize_lane(const RedArgs& r, int l, double s) {
@@ -190,6 +213,12 @@ __device__ void finalize_all(const RedArgs& r) {
           if (qh < r.jobs.n_jobs) {
             c.job[l] = r.jobs.queue[qh++];
             c.state[l] = LS_SEED;
+#ifdef GSK_DEBUG
+            if (!GSK_IDX_OK(c.job[l] >= 0 && c.job[l] < r.jobs.n_jobs, 20, qh - 1)) {
+              c.job[l] = -1;
+              c.state[l] = LS_IDLE;
+            }
+#endif
           } else {
             c.job[l] = -1;
             c.state[l] = LS_IDLE;
@@ -430,18 +459,36 @@ __device__ __forceinline__ void atom_row_product_split(const Layout& g, const ty
   const int lane = threadIdx.x & 31;
   const int grp = lane / (32 / G);
   const int lane0 = (lane % (32 / G)) * L;
+  Ops::zero(acc);
+#ifdef GSK_DEBUG
+  // the atom, its own rows, its neighbour range and its value range (warp-uniform)
+  oI = 0;
+  r0 = 0;
+  if (!GSK_IDX_OK(I >= 0 && I < g.n_atoms, 1, I)) return;
+  {
+    const int o = g.atom_orb[I], rr = g.atom_roff[I];
+    if (!GSK_IDX_OK((o == 1 || o == 4) && rr >= 0 && rr + o <= g.M, 1, I)) return;
+    const int b0 = g.nbr_ptr[I], bm = g.nbr_mid[I], b1 = g.nbr_ptr[I + 1];
+    const int64_t vb0 = g.val_ptr[I];
+    const int64_t nv = o == 4 ? 16 * (int64_t)(bm - b0) + 4 * (int64_t)(b1 - bm) : 4 * (int64_t)(bm - b0) + (b1 - bm);
+    if (!GSK_IDX_OK(b0 >= 0 && b0 <= bm && bm <= b1 && b1 <= g.n_nbr && vb0 >= 0 && vb0 + nv <= g.n_vals, 2, I))
+      return;
+  }
+#endif
   oI = g.atom_orb[I];
   r0 = g.atom_roff[I];
   const TV* v = val + g.val_ptr[I];
   const int e0 = g.nbr_ptr[I];
   const int em = g.nbr_mid[I];
   const int e1 = g.nbr_ptr[I + 1];
-  Ops::zero(acc);
   auto xrow = [&](int r) { return X + (size_t)r * W + lane0; };
   if (oI == 4) {
     for (int base = e0; base < em; base += 32) {
       const int cnt = min(32, em - base);
-      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+#ifdef GSK_DEBUG
+      if (lane < cnt && !GSK_IDX_OK(myr >= 0 && myr + 4 <= g.M, 3, base + lane)) myr = 0;
+#endif
       const TV* vb = v + (size_t)(base - e0) * 16;
       for (int t0 = 0; t0 < cnt; t0 += 2 * G) {
         const int ta = t0 + grp, tb = t0 + G + grp;
@@ -454,7 +501,10 @@ __device__ __forceinline__ void atom_row_product_split(const Layout& g, const ty
     const TV* vh = v + (size_t)(em - e0) * 16;
     for (int base = em; base < e1; base += 32) {
       const int cnt = min(32, e1 - base);
-      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+#ifdef GSK_DEBUG
+      if (lane < cnt && !GSK_IDX_OK(myr >= 0 && myr + 1 <= g.M, 3, base + lane)) myr = 0;
+#endif
       const TV* vb = vh + (size_t)(base - em) * 4;
       for (int t0 = 0; t0 < cnt; t0 += 4 * G) {
 #pragma unroll
@@ -468,7 +518,10 @@ __device__ __forceinline__ void atom_row_product_split(const Layout& g, const ty
   } else {
     for (int base = e0; base < em; base += 32) {
       const int cnt = min(32, em - base);
-      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+#ifdef GSK_DEBUG
+      if (lane < cnt && !GSK_IDX_OK(myr >= 0 && myr + 4 <= g.M, 3, base + lane)) myr = 0;
+#endif
       const TV* vb = v + (size_t)(base - e0) * 4;
       for (int t0 = 0; t0 < cnt; t0 += 2 * G) {
         const int ta = t0 + grp, tb = t0 + G + grp;
@@ -488,7 +541,10 @@ __device__ __forceinline__ void atom_row_product_split(const Layout& g, const ty
     const TV* vh = v + (size_t)(em - e0) * 4;
     for (int base = em; base < e1; base += 32) {
       const int cnt = min(32, e1 - base);
-      const int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+      int myr = lane < cnt ? __ldg(&g.nbr_roff[base + lane]) : 0;
+#ifdef GSK_DEBUG
+      if (lane < cnt && !GSK_IDX_OK(myr >= 0 && myr + 1 <= g.M, 3, base + lane)) myr = 0;
+#endif
       const TV* vb = vh + (base - em);
       const int nq = cnt / 4;
       for (int q0 = 0; q0 < nq; q0 += G) {
@@ -671,6 +727,18 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
+// Shared row of a neighbour entry of a staged tile (checked in the bounds-checked build).
+__device__ __forceinline__ int srow_of(const int16_t* lc, int t, int rows, int x_cap) {
+  const int li = lc[t];
+#ifdef GSK_DEBUG
+  return GSK_IDX_OK(li >= 0 && li + rows <= x_cap, 14, t) ? li : 0;
+#else
+  (void)rows;
+  (void)x_cap;
+  return li;
+#endif
+}
+
 // 16-byte asynchronous global -> shared copy (L2 only), and the arrival on an
 // mbarrier once all of this thread's earlier copies have landed (the arrival
 // is counted in the barrier's expected count).
@@ -707,6 +775,23 @@ struct StageLayout {
   }
 };
 
+#ifdef GSK_DEBUG
+// A tile header whose copies stay inside the tile arrays, the value copy, the
+// stage's buffers and the rows of X, with 16-byte aligned bulk copies.
+__device__ __forceinline__ bool tile_head_ok(const TileHead& hd, const TileArgs& t, int M) {
+  return hd.n_atoms >= 1 && hd.n_atoms <= t.d_cap && hd.d0 >= 0 && hd.d0 + hd.n_atoms <= t.n_desc &&
+         hd.nval >= 0 && hd.nval <= t.v_cap && hd.v0 >= 0 && hd.v0 + hd.nval <= t.n_vals && (hd.v0 & 3) == 0 &&
+         (hd.nval & 3) == 0 && hd.nloc >= 0 && hd.nloc <= t.l_cap && hd.l0 >= 0 && hd.l0 + hd.nloc <= t.n_loc &&
+         (hd.l0 & 7) == 0 && (hd.nloc & 7) == 0 && hd.nbox >= 0 && hd.b0 >= 0 && hd.b0 + hd.nbox <= t.n_box &&
+         hd.n_own >= 0 && hd.n_own <= t.own_cap && hd.r0 >= 0 && hd.r0 + hd.n_own <= M &&
+         hd.wptr[kTileWarps] == hd.n_atoms;
+}
+// A row piece inside X and inside the stage's row buffer.
+__device__ __forceinline__ bool piece_ok(int g0, int rows, int s0, const TileArgs& t, int M) {
+  return rows >= 1 && rows <= kPieceRows && g0 >= 0 && g0 + rows <= M && s0 >= 0 && s0 + rows <= t.x_cap;
+}
+#endif
+
 __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmStagedArgs a) {
   extern __shared__ __align__(128) unsigned char sm_raw[];
   __shared__ double sred[kTileWarps][kMaxW];
@@ -740,7 +825,12 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
     int2 box_next = make_int2(0, 0);
     auto fetch = [&](int j) {
       hd_next = a.t.head[(blockIdx.x + j * gridDim.x) / a.nq];
+#ifdef GSK_DEBUG
+      const int nm = (tile_head_ok(hd_next, a.t, a.g.M) && hd_next.nbox > pw)
+                         ? (hd_next.nbox - pw + kProducers - 1) / kProducers : 0;
+#else
       const int nm = hd_next.nbox > pw ? (hd_next.nbox - pw + kProducers - 1) / kProducers : 0;
+#endif
       box_next = lane < nm ? a.t.box[hd_next.b0 + pw + kProducers * lane] : make_int2(0, 0);
     };
     if (n_mine > 0) fetch(0);
@@ -749,6 +839,13 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
       unsigned char* st = sm_raw + (size_t)s * SL.bytes;
       const TileHead hd = hd_next;
       const int2 box0 = box_next;
+#ifdef GSK_DEBUG
+      const bool hok = (pw == 0 && lane == 0)
+                           ? GSK_IDX_OK(tile_head_ok(hd, a.t, a.g.M), 10, (blockIdx.x + j * gridDim.x) / a.nq)
+                           : tile_head_ok(hd, a.t, a.g.M);
+#else
+      constexpr bool hok = true;
+#endif
       if (j + 1 < n_mine) fetch(j + 1);
       if (j >= 2) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty_bar[s], ((j >> 1) - 1) & 1));  // item j-2 consumed
       if (!ok) break;
@@ -756,31 +853,40 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (pw == 0 && lane == 0) {
         *reinterpret_cast<TileHead*>(st + SL.hdr) = hd;
-        const uint32_t bytes = (uint32_t)hd.nval * sizeof(float) + (uint32_t)hd.nloc * sizeof(int16_t) +
-                               (uint32_t)hd.n_atoms * sizeof(int4);
+        const uint32_t bytes = hok ? (uint32_t)hd.nval * sizeof(float) + (uint32_t)hd.nloc * sizeof(int16_t) +
+                                         (uint32_t)hd.n_atoms * sizeof(int4)
+                                   : 0u;
         mbar_expect_tx(&full_bar[s], bytes);     // releases the header store with the arrival
-        bulk_copy(st + SL.v, a.val + hd.v0, (uint32_t)hd.nval * sizeof(float), &full_bar[s]);
-        bulk_copy(st + SL.l, a.t.loc + hd.l0, (uint32_t)hd.nloc * sizeof(int16_t), &full_bar[s]);
-        bulk_copy(st + SL.d, a.t.desc + hd.d0, (uint32_t)hd.n_atoms * sizeof(int4), &full_bar[s]);
+        if (hok) {
+          bulk_copy(st + SL.v, a.val + hd.v0, (uint32_t)hd.nval * sizeof(float), &full_bar[s]);
+          bulk_copy(st + SL.l, a.t.loc + hd.l0, (uint32_t)hd.nloc * sizeof(int16_t), &full_bar[s]);
+          bulk_copy(st + SL.d, a.t.desc + hd.d0, (uint32_t)hd.n_atoms * sizeof(int4), &full_bar[s]);
+        }
       }
       // row union of X: 4 rows x 8 chunks of 16 bytes per warp instruction; this
       // warp copies boxes pw, pw + kProducers, ... (32 of them per register load)
       float* sX = reinterpret_cast<float*>(st + SL.x);
       float* sP = reinterpret_cast<float*>(st + SL.p);
       float* sYs = reinterpret_cast<float*>(st + SL.y);
-      const int nmine = hd.nbox > pw ? (hd.nbox - pw + kProducers - 1) / kProducers : 0;
+      const int nmine = (hok && hd.nbox > pw) ? (hd.nbox - pw + kProducers - 1) / kProducers : 0;
       if (a.nq == 1) {
         // 32 lanes: a piece of a row run is contiguous in X, one bulk copy per piece
         for (int k0 = 0; k0 < nmine; k0 += 32) {
           int2 mybox = box0;
           if (k0 > 0) mybox = (k0 + lane < nmine) ? a.t.box[hd.b0 + pw + kProducers * (k0 + lane)] : make_int2(0, 0);
+#ifdef GSK_DEBUG
+          if (k0 + lane < nmine &&
+              GSK_IDX_OK(piece_ok(mybox.x, mybox.y >> 16, mybox.y & 0xffff, a.t, a.g.M), 11,
+                         hd.b0 + pw + kProducers * (k0 + lane))) {
+#else
           if (k0 + lane < nmine) {
+#endif
             const uint32_t bytes = (uint32_t)(kTileLanes * sizeof(float)) * (uint32_t)(mybox.y >> 16);
             mbar_add_tx(&full_bar[s], bytes);
             bulk_copy(sX + (mybox.y & 0xffff) * kTileLanes, a.X + (size_t)mybox.x * kTileLanes, bytes, &full_bar[s]);
           }
         }
-        if (pw == 1 && lane < 2) {
+        if (hok && pw == 1 && lane < 2) {
           const uint32_t bytes = (uint32_t)hd.n_own * kTileLanes * sizeof(float);
           mbar_add_tx(&full_bar[s], bytes);
           bulk_copy(lane == 0 ? sP : sYs, (lane == 0 ? a.P : a.Y) + (size_t)hd.r0 * kTileLanes, bytes, &full_bar[s]);
@@ -794,12 +900,15 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
             const int g0 = __shfl_sync(0xffffffffu, mybox.x, k);
             const int code = __shfl_sync(0xffffffffu, mybox.y, k);
             const int hgt = code >> 16, s0 = code & 0xffff;
+#ifdef GSK_DEBUG
+            if (!GSK_IDX_OK(piece_ok(g0, hgt, s0, a.t, a.g.M), 11, hd.b0 + pw + kProducers * (k0 + k))) continue;
+#endif
             for (int r = sub; r < hgt; r += 4)
               cp_async16(sX + (s0 + r) * kTileLanes + ch, a.X + (size_t)(g0 + r) * a.W + qlane + ch);
           }
         }
         // own rows of P and Y
-        for (int r = pw * 4 + sub; r < hd.n_own; r += 4 * kProducers) {
+        for (int r = pw * 4 + sub; hok && r < hd.n_own; r += 4 * kProducers) {
           const size_t g = (size_t)(hd.r0 + r) * a.W + qlane + ch;
           cp_async16(sP + r * kTileLanes + ch, a.P + g);
           cp_async16(sYs + r * kTileLanes + ch, a.Y + g);
@@ -836,12 +945,30 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
       const int4* sD = reinterpret_cast<const int4*>(st + SL.d);
       const int r0 = shd->r0;
       const int k1 = shd->wptr[warp + 1];
-      for (int k = shd->wptr[warp]; k < k1; ++k) {
+#ifdef GSK_DEBUG
+      // the warp's list inside the tile's descriptors (else the list is skipped)
+      const int kb = GSK_IDX_OK(shd->wptr[warp] <= k1 && k1 <= shd->n_atoms && k1 <= a.t.d_cap, 12, warp)
+                         ? (int)shd->wptr[warp] : k1;
+#else
+      const int kb = shd->wptr[warp];
+#endif
+      for (int k = kb; k < k1; ++k) {
         const int4 d = sD[k];
         const int oI = d.x & 0xff;
         const int prow = (d.x >> 8) & 0xff;
         const int xown = d.x >> 16;
         const int n4 = d.y & 0xffff, n1 = d.y >> 16;
+#ifdef GSK_DEBUG
+        {
+          // the atom's own rows, values and neighbour indices inside the stage (warp-uniform)
+          const int nv = oI == 4 ? 16 * n4 + 4 * n1 : 4 * n4 + n1;
+          const bool ok = (oI == 4 || (oI == 1 && (n1 & 3) == 0)) && prow + oI <= shd->n_own &&
+                          shd->n_own <= a.t.own_cap && r0 >= 0 && r0 + prow + oI <= a.g.M && xown >= 0 &&
+                          xown + oI <= a.t.x_cap && d.z >= 0 && d.z + nv <= shd->nval && shd->nval <= a.t.v_cap &&
+                          d.w >= 0 && d.w + n4 + n1 <= shd->nloc && shd->nloc <= a.t.l_cap;
+          if (!GSK_IDX_OK(ok, 13, k)) continue;
+        }
+#endif
         const float* v = sV + d.z;
         const int16_t* lc = sL + d.w;
         float acc[4][4];
@@ -852,7 +979,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
         if (oI == 4) {
 #pragma unroll 2
           for (int t = grp; t < n4; t += 4) {
-            const float* xp = sX + lc[t] * kTileLanes + lane0;
+            const float* xp = sX + srow_of(lc, t, 4, a.t.x_cap) * kTileLanes + lane0;
             const float4 x0 = lds4(xp), x1 = lds4(xp + kTileLanes), x2 = lds4(xp + 2 * kTileLanes),
                          x3 = lds4(xp + 3 * kTileLanes);
             const float* vb = v + t * 16;
@@ -862,13 +989,13 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
             fma_col(acc, lds4(vb), x0);
           }
           const float* vh = v + n4 * 16;
-#pragma unroll 2
+#pragma unroll 4
           for (int t = grp; t < n1; t += 4)
-            fma_col(acc, lds4(vh + t * 4), lds4(sX + lc[n4 + t] * kTileLanes + lane0));
+            fma_col(acc, lds4(vh + t * 4), lds4(sX + srow_of(lc, n4 + t, 1, a.t.x_cap) * kTileLanes + lane0));
         } else {
-#pragma unroll 2
+#pragma unroll 4
           for (int t = grp; t < n4; t += 4) {
-            const float* xp = sX + lc[t] * kTileLanes + lane0;
+            const float* xp = sX + srow_of(lc, t, 4, a.t.x_cap) * kTileLanes + lane0;
             const float4 c = lds4(v + t * 4);
             const float4 x0 = lds4(xp), x1 = lds4(xp + kTileLanes), x2 = lds4(xp + 2 * kTileLanes),
                          x3 = lds4(xp + 3 * kTileLanes);
@@ -880,12 +1007,14 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
           }
           const float* vh = v + n4 * 4;
           const int nqd = n1 / 4;
-#pragma unroll 2
+#pragma unroll 4
           for (int qd = grp; qd < nqd; qd += 4) {
             const int16_t* lq = lc + n4 + 4 * qd;
             const float4 c = lds4(vh + 4 * qd);
-            const float4 x0 = lds4(sX + lq[0] * kTileLanes + lane0), x1 = lds4(sX + lq[1] * kTileLanes + lane0),
-                         x2 = lds4(sX + lq[2] * kTileLanes + lane0), x3 = lds4(sX + lq[3] * kTileLanes + lane0);
+            const float4 x0 = lds4(sX + srow_of(lq, 0, 1, a.t.x_cap) * kTileLanes + lane0),
+                         x1 = lds4(sX + srow_of(lq, 1, 1, a.t.x_cap) * kTileLanes + lane0),
+                         x2 = lds4(sX + srow_of(lq, 2, 1, a.t.x_cap) * kTileLanes + lane0),
+                         x3 = lds4(sX + srow_of(lq, 3, 1, a.t.x_cap) * kTileLanes + lane0);
             const float a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w},
                         a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
 #pragma unroll
@@ -1069,7 +1198,19 @@ __global__ void __launch_bounds__(kThreads) k_update(const VecArgs a) {
     st[i] = c.state[l];
     al[i] = c.alpha[l];
     bp[i] = c.beta_prev[l];
+#ifdef GSK_DEBUG
+    // the job index, then its row of e_j, each checked before use
+    jr[i] = -1;
+    if (st[i] == LS_SEED) {
+      const int jb = c.job[l];
+      if (GSK_IDX_OK(jb >= 0 && jb < a.red.jobs.n_jobs, 21, jb)) {
+        jr[i] = a.red.jobs.col_row[jb];
+        if (!GSK_IDX_OK(jr[i] >= 0 && jr[i] < a.M, 22, jb)) jr[i] = -1;
+      }
+    }
+#else
     jr[i] = (st[i] == LS_SEED) ? a.red.jobs.col_row[c.job[l]] : -1;
+#endif
   }
   const int slot = (*a.step) & 1;
   const double* Bq = slot ? a.ring1 : a.ring0;
@@ -1251,7 +1392,19 @@ __global__ void __launch_bounds__(kThreads) k_update_df(const VecArgs a) {
     st[i] = c.state[l];
     al[i] = df_from_double(c.alpha[l]);
     bp[i] = df_from_double(c.beta_prev[l]);
+#ifdef GSK_DEBUG
+    // the job index, then its row of e_j, each checked before use
+    jr[i] = -1;
+    if (st[i] == LS_SEED) {
+      const int jb = c.job[l];
+      if (GSK_IDX_OK(jb >= 0 && jb < a.red.jobs.n_jobs, 21, jb)) {
+        jr[i] = a.red.jobs.col_row[jb];
+        if (!GSK_IDX_OK(jr[i] >= 0 && jr[i] < a.M, 22, jb)) jr[i] = -1;
+      }
+    }
+#else
     jr[i] = (st[i] == LS_SEED) ? a.red.jobs.col_row[c.job[l]] : -1;
+#endif
   }
   const int slot = (*a.step) & 1;
   const float2* Bq = reinterpret_cast<const float2*>(slot ? a.ring1 : a.ring0);
@@ -1398,6 +1551,9 @@ struct ShiftArgs {
   double* out_resid;
   double tol;
   int max_iter;
+#ifdef GSK_DEBUG
+  int M;                    // rows of q (pattern rows are checked against it)
+#endif
 };
 
 __global__ void __launch_bounds__(kThreads) k_shift(const ShiftArgs a) {
@@ -1411,6 +1567,11 @@ __global__ void __launch_bounds__(kThreads) k_shift(const ShiftArgs a) {
   __shared__ int s_bad;
   const int S = a.S;
   const int job = c.job[lane];
+#ifdef GSK_DEBUG
+  if (!GSK_IDX_OK(job >= 0 && job < a.jobs.n_jobs, 21, job)) return;
+  if (!GSK_IDX_OK(a.job_off[job + 1] - a.job_off[job] <= a.Pmax && a.job_off[job] <= a.job_off[job + 1], 23, job))
+    return;
+#endif
   const int nprev = c.n[lane];
   const int n = nprev + 1;                 // step processed now
   const int brk = c.brk[lane];
@@ -1479,7 +1640,12 @@ __global__ void __launch_bounds__(kThreads) k_shift(const ShiftArgs a) {
     const size_t e = (size_t)i * S + k;
     double2 xv;
     if (!bad) {
+#ifdef GSK_DEBUG
+      const int pr = a.prow[off + i];
+      const size_t qidx = (size_t)(GSK_IDX_OK(pr >= 0 && pr < a.M, 24, off + i) ? pr : 0) * a.W + lane;
+#else
       const size_t qidx = (size_t)a.prow[off + i] * a.W + lane;
+#endif
       double qi;
       if (a.q_df) {
         const float2 qq = reinterpret_cast<const float2*>(a.q)[qidx];
@@ -1530,6 +1696,12 @@ __global__ void k_prime(const PrimeArgs a) {
     if (l < a.jobs.n_jobs) {
       c.job[l] = a.jobs.queue[l];
       c.state[l] = LS_SEED;
+#ifdef GSK_DEBUG
+      if (!GSK_IDX_OK(c.job[l] >= 0 && c.job[l] < a.jobs.n_jobs, 20, l)) {
+        c.job[l] = -1;
+        c.state[l] = LS_IDLE;
+      }
+#endif
     } else {
       c.job[l] = -1;
       c.state[l] = LS_IDLE;
@@ -1576,6 +1748,10 @@ __global__ void k_wrapup(const WrapArgs a) {
     const LaneCtl& c = a.c;
     if (c.state[lane] == LS_ACTIVE && !c.done[lane]) {
       const int job = c.job[lane];
+#ifdef GSK_DEBUG
+      if (!GSK_IDX_OK(job >= 0 && job < a.jobs.n_jobs, 21, job)) return;
+      if (!GSK_IDX_OK(a.job_off[job + 1] - a.job_off[job] <= a.Pmax, 23, job)) return;
+#endif
       const int64_t off = a.job_off[job];
       const int P = (int)(a.job_off[job + 1] - off);
       const double2* xb = a.xbuf + (size_t)lane * a.Pmax * a.S;
@@ -2166,9 +2342,19 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   P.nsplit = std::max(1, std::min(8, (h->num_sms * 2) / W));
   P.sh = ShiftArgs{c, jobs, W, S, Pmax, P.nsplit, d_eps, d_eps + S, eta ? 1 : 0, d_job_off, d_prow, pbuf, xbuf, dgb, q, P.df ? 1 : 0, Gd,
                    d_iters, d_status, d_resid, opt.tol, opt.max_iter};
+#ifdef GSK_DEBUG
+  P.sh.M = h->M;
+#endif
   P.prime = PrimeArgs{c, jobs, gc, W};
   P.wrap = WrapArgs{c, jobs, W, S, Pmax, d_job_off, xbuf, Gd, d_iters, d_status, d_resid};
 
+#ifdef GSK_DEBUG
+  {
+    const int zero[4] = {0, 0, 0, 0};
+    if (cudaMemcpyToSymbolAsync(g_dbg, zero, sizeof(zero), 0, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      return GSK_ECUDA;
+  }
+#endif
   // ---- run ----
   auto run = [&](auto Ltag) -> cudaError_t {
     constexpr int LL = decltype(Ltag)::value;
@@ -2208,8 +2394,15 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_rs.data(), d_resid, n_cols * sizeof(double), cudaMemcpyDeviceToHost, stream);
   int h_cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, c.queue_head, 9 * sizeof(int), cudaMemcpyDeviceToHost, stream);
+  int h_dbg[4] = {0, 0, 0, 0};
+#ifdef GSK_DEBUG
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(h_dbg, g_dbg, sizeof(h_dbg), 0, cudaMemcpyDeviceToHost, stream);
+#endif
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GSK_ECUDA;
+  h->last.debug_code = h_dbg[0];
+  h->last.debug_index = ((int64_t)h_dbg[2] << 32) | (int64_t)(uint32_t)h_dbg[1];
+  if (h_dbg[0] != 0) return GSK_EBOUNDS;      // bounds-checked build: an index check failed
   if (h_cnt[8] != 0) return GSK_ETIMEOUT;     // a bounded wait of the staged SpMM gave up
   {
     // scal layout: queue_head, cg_iter, step, unfinished, cg_total
@@ -2235,6 +2428,25 @@ int solve_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int32_
 // ===========================================================================
 namespace gsk {
 
+#ifdef GSK_DEBUG
+// Clear the record of failed index checks (before a call's kernels).
+int dbg_reset(cudaStream_t s) {
+  const int zero[4] = {0, 0, 0, 0};
+  return cudaMemcpyToSymbolAsync(g_dbg, zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s) == cudaSuccess ? GSK_OK
+                                                                                                       : GSK_ECUDA;
+}
+// Wait for the call's kernels and report the first failed index check.
+int dbg_collect(gsk_ctx* h, cudaStream_t s) {
+  int d[4] = {0, 0, 0, 0};
+  if (cudaMemcpyFromSymbolAsync(d, g_dbg, sizeof(d), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return GSK_ECUDA;
+  h->last.debug_code = d[0];
+  h->last.debug_index = ((int64_t)d[2] << 32) | (int64_t)(uint32_t)d[1];
+  return d[0] != 0 ? GSK_EBOUNDS : GSK_OK;
+}
+#endif
+
 int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const void* X, void* Y, int32_t n_rep,
               void* stream) {
   if (which < 0 || which > 2 || (precision != GSK_FP64 && precision != GSK_MIXED) || n_rep < 0 || !X || !Y)
@@ -2244,6 +2456,9 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
   if (which == 2 && (precision != GSK_MIXED || h->tiles.n_tiles == 0)) return GSK_ENOTSUP;
   if (cudaSetDevice(h->device) != cudaSuccess) return GSK_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+#ifdef GSK_DEBUG
+  if (dbg_reset(s) != GSK_OK) return GSK_ECUDA;
+#endif
   const int nq = W / kTileLanes;
   int grid_t = std::min(h->tiles.n_tiles * nq, h->num_sms);
   grid_t = std::max(nq, grid_t - grid_t % nq);
@@ -2297,6 +2512,12 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
     if (cudaMemcpyAsync(&herr, c.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return GSK_ECUDA;
+#ifdef GSK_DEBUG
+    {
+      const int dr = dbg_collect(h, s);
+      if (dr != GSK_OK) return dr;
+    }
+#endif
     return herr ? GSK_ETIMEOUT : GSK_OK;
   }
   for (int i = 0; i < n_rep; ++i) {
@@ -2327,7 +2548,11 @@ int spmm_impl(gsk_ctx* h, int32_t which, int32_t precision, int32_t W, const voi
     }
     if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
   }
+#ifdef GSK_DEBUG
+  return dbg_collect(h, s);     // the bounds-checked build waits here to report failed checks
+#else
   return GSK_OK;
+#endif
 }
 
 // Bytes of the reduction workspace that spmm64_dot needs (zero it once
@@ -2488,3 +2713,32 @@ int autotune_impl(gsk_ctx* h, int32_t S, const double* z, const double* eta, int
 }
 
 }  // namespace gsk
+
+// ===========================================================================
+// Self-test of the bounds-checked build's recording path
+// ===========================================================================
+namespace gsk {
+#ifdef GSK_DEBUG
+__global__ void k_dbg_selftest(int code, long long idx) {
+  if (threadIdx.x == 0) (void)GSK_IDX_OK(false, code, idx);     // a check that fails, guarding no access
+}
+#endif
+}  // namespace gsk
+
+extern "C" int gsk_debug_selftest(int32_t* code, int64_t* index) {
+  if (!code || !index) return GSK_EINVAL;
+#ifdef GSK_DEBUG
+  if (gsk::dbg_reset(0) != GSK_OK) return GSK_ECUDA;
+  gsk::k_dbg_selftest<<<1, 32>>>(99, 12345678901LL);
+  if (cudaGetLastError() != cudaSuccess) return GSK_ECUDA;
+  int d[4] = {0, 0, 0, 0};
+  if (cudaMemcpyFromSymbol(d, gsk::g_dbg, sizeof(d)) != cudaSuccess) return GSK_ECUDA;
+  *code = d[0];
+  *index = ((int64_t)d[2] << 32) | (int64_t)(uint32_t)d[1];
+  return gsk::dbg_reset(0) == GSK_OK && cudaDeviceSynchronize() == cudaSuccess ? GSK_OK : GSK_ECUDA;
+#else
+  *code = 0;
+  *index = 0;
+  return GSK_ENOTSUP;
+#endif
+}

@@ -201,6 +201,12 @@ int build_tiles(gsk_ctx* h, const std::vector<int32_t>& roff, const std::vector<
   t.loc = h->d_loc.as<int16_t>();
   t.desc = h->d_desc.as<int4>();
   t.order = h->d_order.as<int32_t>();
+#ifdef GSK_DEBUG
+  t.n_box = (int32_t)P.box.size();
+  t.n_loc = (int32_t)P.loc.size();
+  t.n_desc = (int32_t)P.desc.size();
+  t.n_vals = n_vals;
+#endif
   h->tile_boxes = (int64_t)P.box.size();
   return GSK_OK;
 }

@@ -14,9 +14,12 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libgsk.so")
+# GSK_DEBUG=1 in the environment loads the bounds-checked build (build.build(debug=True))
+DEBUG_BUILD = os.environ.get("GSK_DEBUG", "0") == "1"
+LIB_PATH = os.path.join(_PKG, "libgsk_debug.so" if DEBUG_BUILD else "libgsk.so")
 
 GSK_OK, GSK_EINVAL, GSK_ENOTSPD, GSK_ENOMEM, GSK_ECUDA, GSK_ETIMEOUT, GSK_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+GSK_EBOUNDS = -7
 GSK_CONVERGED, GSK_NOT_CONVERGED, GSK_BREAKDOWN, GSK_TIMEOUT = 0, 1, 2, 3
 GSK_FP64, GSK_MIXED, GSK_MIXED_DF = 0, 1, 2
 GSK_SCHED_FIFO, GSK_SCHED_LEARNED = 0, 1
@@ -31,7 +34,8 @@ class GskError(RuntimeError):
 
 class Stats(C.Structure):
     _fields_ = [("outer_steps", C.c_int64), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64),
-                ("batch_w", C.c_int32), ("used_graph", C.c_int32), ("spmm_kernel", C.c_int32)]
+                ("batch_w", C.c_int32), ("used_graph", C.c_int32), ("spmm_kernel", C.c_int32),
+                ("debug_code", C.c_int32), ("debug_index", C.c_int64)]
 
 
 class _Csr(C.Structure):
@@ -51,7 +55,8 @@ class Options(C.Structure):
 
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libgsk.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        how = "build.build(debug=True)" if DEBUG_BUILD else "__graft_entry__.build()"
+        raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run {how}")
     lib = C.CDLL(LIB_PATH)
     P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     sig = {
@@ -83,6 +88,7 @@ def _load() -> C.CDLL:
         "gsk_marnoldi": (C.c_int, [P, I32, P, I32, D, D, P, I32, P, P, P, P, P, P]),
         "gsk_mu_from_traces": (C.c_int, [P, I32, P, P, P, D, D, D, D, P, P]),
         "gsk_marnoldi_projected": (C.c_int, [P, P, I32, I32, P, I32, D, D, P, P, P, P, P, P]),
+        "gsk_debug_selftest": (C.c_int, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -96,6 +102,14 @@ _lib = _load()
 
 def lib() -> C.CDLL:
     return _lib
+
+
+def debug_selftest() -> tuple[int, int, int]:
+    """gsk_debug_selftest: (status, code, index); GSK_ENOTSUP outside the bounds-checked build."""
+    code = C.c_int32()
+    idx = C.c_int64()
+    rc = _lib.gsk_debug_selftest(C.byref(code), C.byref(idx))
+    return int(rc), int(code.value), int(idx.value)
 
 
 def strerror(code: int) -> str:

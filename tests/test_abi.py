@@ -144,3 +144,19 @@ def test_per_column_values_are_marshalled_to_n_entries(libgsk):
         g._per_column(np.array([0.1, 0.2]), 3)
     with pytest.raises(ValueError):
         g._per_column(np.zeros((3, 1)), 3)
+
+
+def test_bounds_checked_build_links_and_exports(libgsk):
+    """The -DGSK_DEBUG build (libgsk_debug.so) compiles for sm_103a and
+    exports the same entry points; the normal build answers the self-test
+    with GSK_ENOTSUP before touching the GPU."""
+    from paper_1609_08377_gb300 import build
+
+    path = build.build(debug=True)
+    assert path.endswith("libgsk_debug.so") and os.path.exists(path)
+    dbg = C.CDLL(path)
+    for name in _declared("gsk.h"):
+        assert hasattr(dbg, name), name
+    dbg.gsk_strerror.restype = C.c_char_p
+    assert b"index check" in dbg.gsk_strerror(libgsk.GSK_EBOUNDS)
+    assert libgsk.debug_selftest() == (libgsk.GSK_ENOTSUP, 0, 0)
