@@ -989,11 +989,11 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
             fma_col(acc, lds4(vb), x0);
           }
           const float* vh = v + n4 * 16;
-#pragma unroll 4
+#pragma unroll 2
           for (int t = grp; t < n1; t += 4)
             fma_col(acc, lds4(vh + t * 4), lds4(sX + srow_of(lc, n4 + t, 1, a.t.x_cap) * kTileLanes + lane0));
         } else {
-#pragma unroll 4
+#pragma unroll 2
           for (int t = grp; t < n4; t += 4) {
             const float* xp = sX + srow_of(lc, t, 4, a.t.x_cap) * kTileLanes + lane0;
             const float4 c = lds4(v + t * 4);
@@ -1007,7 +1007,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_spmm_staged(const SpmmSta
           }
           const float* vh = v + n4 * 4;
           const int nqd = n1 / 4;
-#pragma unroll 4
+#pragma unroll 2
           for (int qd = grp; qd < nqd; qd += 4) {
             const int16_t* lq = lc + n4 + 4 * qd;
             const float4 c = lds4(vh + 4 * qd);
